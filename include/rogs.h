@@ -1,0 +1,226 @@
+/*
+ * rogs.h -- C-ABI of librogs: GB300-native (sm_103a) differentiable splatting
+ * of meshgrid Gaussian surfels (RoGs, arXiv 2405.14342).
+ *
+ * Pointers are plain host or device addresses as stated per argument; sizes
+ * are element counts.  No call allocates device memory except rogs_create,
+ * rogs_reserve and (when a call needs more scratch than it holds)
+ * the first call of a given size; every call is asynchronous on the given
+ * stream unless it says it synchronises.  The caller owns every buffer it
+ * passes; the library owns only the scratch held in its context.  One
+ * context must not be used from two streams at once (its scratch is shared).
+ *
+ * Errors: every call returns a rogs_status; rogs_last_error() gives a
+ * one-line message for the last failing call on that context.  Argument
+ * errors are detected on the host (ROGS_ERR_INVALID) before anything is
+ * launched.  A data-dependent overflow (more visible surfels or tile pairs
+ * than the configured capacities) cannot be seen on the host without a
+ * synchronisation: it is recorded in the state header (status word) and
+ * returned as ROGS_ERR_CAPACITY by rogs_state_counts(); the frame's outputs
+ * are then incomplete and must be recomputed with larger capacities.
+ */
+#ifndef ROGS_H
+#define ROGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rogs_ctx rogs_ctx;
+typedef void* rogs_stream; /* a cudaStream_t; NULL = the legacy default stream */
+
+typedef enum {
+    ROGS_OK = 0,
+    ROGS_ERR_INVALID = 1,   /* bad argument, detected on the host */
+    ROGS_ERR_CAPACITY = 2,  /* record or pair capacity exceeded (device-detected) */
+    ROGS_ERR_OOM = 3,       /* device allocation failed / admission refused */
+    ROGS_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+    ROGS_ERR_TIMEOUT = 5,   /* a bounded device or host wait gave up */
+    ROGS_ERR_BUSY = 6,      /* no free serving slot */
+    ROGS_ERR_NOT_READY = 7  /* serving request not finished yet */
+} rogs_status;
+
+enum { ROGS_PERSP = 0, ROGS_ORTHO = 1 };
+
+#define ROGS_MAX_VIEWS 128   /* views per render call */
+#define ROGS_MAX_CLASSES 54  /* C, semantic logits per surfel */
+
+/* Rendering constants.  Defaults (rogs_default_config): tile 16x16,
+   t_min 1e-4, alpha_min 1/255, alpha_max 0.99, eps 0.3 px^2, near 0.2 m,
+   box 20 m / 40 m, jac_clamp 1.3. */
+typedef struct {
+    int32_t tile_w, tile_h;     /* 16x16, 32x8 or 8x8 pixels */
+    int32_t num_classes;        /* C in [0, ROGS_MAX_CLASSES] */
+    float t_min;                /* stop before T would fall below this (Eq. 6) */
+    float alpha_min;            /* a surfel counts at a pixel iff a >= alpha_min */
+    float alpha_max;            /* a = min(alpha_max, alpha * g) */
+    float eps_dilate;           /* px^2 added to the 2D covariance diagonal */
+    float near_plane;           /* perspective: keep iff binary32 depth > near */
+    float box_half_x;           /* perspective box cull: |lateral| <= box_half_x (m) */
+    float box_depth;            /* and 0 <= forward <= box_depth (m) */
+    float jac_clamp;            /* EWA Jacobian evaluated at x/z clamped to +-jac_clamp*W/(2 fx) */
+    int64_t record_capacity;    /* visible (view, surfel) records per render call */
+    int64_t pair_capacity;      /* (tile, record) pairs per render call (<= 2^32-1) */
+} rogs_config;
+
+/* One camera.  p_cam = R_wc p_world + t_wc, camera axes x right, y down, z
+   forward.  Perspective: u = fx x/z + cx.  Orthographic: u = fx x + cx
+   (fx in px per metre).  exposure_idx selects (a, b) of Eq. 7.
+   use_box_cull enables the supplementary's perspective box (ignored for
+   orthographic cameras). */
+typedef struct {
+    int32_t kind, width, height, exposure_idx, use_box_cull, reserved;
+    float fx, fy, cx, cy;
+    float R_wc[9]; /* row-major */
+    float t_wc[3];
+} rogs_camera;
+
+/* Surfel map (Sec. 3.1, Eq. 3), device pointers, FP32, row-major:
+   xyz [n,3], scale [n,2] = (s_x, s_y) (s_z = 0), quat [n,4] = (w,x,y,z)
+   (normalised inside), opacity [n] = alpha, rgb [n,3], sem [n,C] logits. */
+typedef struct {
+    const float *xyz, *scale, *quat, *opacity, *rgb, *sem;
+    int64_t n;
+} rogs_surfels;
+
+/* Gradient buffers (device, FP32, same shapes as rogs_surfels plus
+   exposure [n_exposure,2]).  rogs_render_bwd ADDS into them.  Any pointer
+   may be NULL to skip that gradient. */
+typedef struct {
+    float *xyz, *scale, *quat, *opacity, *rgb, *sem, *exposure;
+} rogs_grads;
+
+/* Counters written by the device into the state header. */
+typedef struct {
+    uint64_t n_records;      /* visible (view, surfel) records (clamped to capacity) */
+    uint64_t n_pairs;        /* (tile, record) pairs (clamped to capacity) */
+    uint64_t need_records;   /* records the frame needed */
+    uint64_t need_pairs;     /* pairs the frame needed */
+    uint64_t composited;     /* (pixel, surfel) pairs composited by the forward */
+    uint32_t status;         /* bit 0 record overflow, bit 1 pair overflow */
+    uint32_t n_views;
+} rogs_counts;
+
+/* Byte offsets of the sections of a render state (device buffer filled by
+   rogs_render_fwd and read by rogs_render_bwd).  Pixels of view v start at
+   pixel offset pix_base[v] = sum of earlier views' W*H; tiles of view v at
+   tile_base[v].  Sections:
+     header      rogs_counts
+     records     48-byte records: float mean_int[2], mean_frac[2], conic[3]
+                 (A,B,C of the inverse 2D covariance), alpha, depth (camera z),
+                 key (binary32 sort depth), uint32 surfel, uint32 view;
+                 ordered by (view, surfel)
+     rects       uint32[2] per record: tx0 | ty0<<16, tx1 | ty1<<16 (inclusive)
+     pair_rec    uint32 per pair: record id, ordered by (view, tile, key, surfel)
+     tile_range  uint32[2] per tile: [start, end) into pair_rec
+     pix_T       float per pixel: final transmittance
+     pix_last    uint32 per pixel: entries of its tile list up to and including
+                 the last composited one */
+typedef struct {
+    uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, total_bytes;
+    int64_t total_tiles, total_pixels;
+} rogs_state_layout;
+
+/* ---------------------------------------------------------- context */
+
+/* Fill *cfg with the defaults above for C classes and the given capacities. */
+rogs_status rogs_default_config(int32_t num_classes, int64_t record_capacity, int64_t pair_capacity,
+                                rogs_config* cfg);
+
+/* Create a context on the current CUDA device.  Allocates scratch for the
+   configured capacities (device memory, owned by the context). */
+rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out);
+
+/* Release the context and its scratch.  Synchronises the device. */
+void rogs_destroy(rogs_ctx* ctx);
+
+/* Last error message of this context ("" if none).  Valid until the next call. */
+const char* rogs_last_error(const rogs_ctx* ctx);
+
+/* Pre-size scratch for maps of up to n_surfels and up to n_views views so
+   that later calls (e.g. inside CUDA-graph capture) never allocate. */
+rogs_status rogs_reserve(rogs_ctx* ctx, int64_t n_surfels, int32_t n_views);
+
+/* Output and state geometry of a set of cameras (host-side arithmetic).
+   out_elems = (3 + C + 1) * total pixels floats: view v occupies
+   [(3+C+1) * pix_base[v], ...) laid out as planes [3+C+1][H][W] = rgb after
+   exposure (Eq. 7), sem[C], depth (sum of w * camera z). */
+rogs_status rogs_state_layout_of(const rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views,
+                                 rogs_state_layout* layout, uint64_t* out_elems);
+
+/* Copy the state header to the host (synchronises `stream`).  Returns
+   ROGS_ERR_CAPACITY if the frame overflowed a capacity, else ROGS_OK. */
+rogs_status rogs_state_counts(rogs_ctx* ctx, const void* state, rogs_counts* counts, rogs_stream stream);
+
+/* ---------------------------------------------------------- the path */
+
+/* Pose-based initialisation (Sec. 3.2, Eq. 4; supplementary Eqs. S1-S2).
+   For each grid point (x_i, y_i) find the nearest pose in xy (binary32
+   squared distance, ties to the lowest pose index) and set
+     z_i = z_v - (n31 (x_i - x_v) + n32 (y_i - y_v)) / n33      (exact_plane = 1)
+     z_i = z_v                                                 (exact_plane = 0)
+   with n3 the third column of R_v, and R_i = R_v as a unit quaternion
+   (w,x,y,z), w >= 0.
+   grid_xy: device [n,2]; poses: HOST [n_poses,12] = (x,y,z, R_v row-major);
+   out_z: device [n]; out_quat: device [n,4]; out_nearest: device [n] or NULL.
+   ROGS_ERR_INVALID if n_poses < 1 or some pose has |n33| < 1e-6 while
+   exact_plane = 1.  Synchronises the host copy of the poses. */
+rogs_status rogs_init_from_poses(rogs_ctx* ctx, const float* grid_xy, int64_t n, const float* poses,
+                                 int64_t n_poses, int32_t exact_plane, float* out_z, float* out_quat,
+                                 int32_t* out_nearest, rogs_stream stream);
+
+/* Forward render of n_views cameras in one pass (Sec. 3.3.1, Eqs. 2, 5, 6, 7
+   and the supplementary box cull):
+     1. cull + EWA projection of every surfel into every view,
+     2. tile binning and hand-written radix sorts: pairs ordered by
+        (view, tile, binary32 depth, surfel index),
+     3. per-tile front-to-back compositing of rgb, C semantic logits and depth
+        with the transmittance stop, then the exposure of Eq. 7.
+   cams: HOST [n_views]; exposure_ab: device [n_exposure,2] (a, b);
+   out: device float[out_elems] (rogs_state_layout_of); state: device buffer
+   of layout.total_bytes, 256-byte aligned, written here and read by
+   rogs_render_bwd.  ROGS_ERR_INVALID for n_views outside [1, ROGS_MAX_VIEWS],
+   a camera with non-positive size or focal length, or an exposure index
+   outside [0, n_exposure). */
+rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
+                            int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
+                            void* state, rogs_stream stream);
+
+/* Masked L1 colour + masked cross-entropy semantic loss (Sec. 3.3.2, Eqs. 8,
+   9), weighted by lambda_c and lambda_s (Eq. 12), over all views' pixels:
+     L = lambda_c/|M| sum_i m_i sum_rgb |c'_i - cbar_i|
+       + lambda_s/|M| sum_i m_i CE(softmax(sem_i), label_i)
+   |M| = number of mask pixels (L = 0 and zero gradient if |M| = 0).
+   out: the forward output; tgt_rgb: device [3][pixels] planes per view (same
+   pixel offsets as out); label: device int32 [pixels] in [0, C); mask:
+   device uint8 [pixels] (a label outside [0, C) drops that pixel's semantic term).  Writes loss: device float[1] and grad_out: device
+   float[out_elems] = dL/dout (depth plane zero; sign(0) = 0 for L1). */
+rogs_status rogs_loss(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, const float* out,
+                      const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
+                      float lambda_s, float* loss, float* grad_out, rogs_stream stream);
+
+/* Backward of rogs_render_fwd (the adjoint of Eqs. 2, 5, 6, 7): reverse
+   traversal of each tile's list from each pixel's last composited entry,
+   recovering T by division, then the chain through the EWA projection.
+   grad_out: device float[out_elems] = dL/dout.  Gradients are ADDED into
+   `grads` (device; zero them first for a plain gradient).  state must be the
+   one filled by the forward with the same surfels, cameras and exposure. */
+rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
+                            int32_t n_views, const float* exposure_ab, int32_t n_exposure, const void* state,
+                            const float* grad_out, const rogs_grads* grads, rogs_stream stream);
+
+/* Stable LSD radix sort of (key, value) pairs of uint32 on key bits
+   [0, key_bits) -- the sort used inside rogs_render_fwd, exposed for
+   testing and reuse.  All pointers device; inputs are not modified; n <=
+   the context's pair capacity. */
+rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
+                            int32_t key_bits, uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROGS_H */

@@ -1,0 +1,523 @@
+// api.cu -- the C-ABI of librogs (declared in include/rogs.h): argument
+// checks, per-view parameter derivation, scratch management and the launch
+// sequences of the forward, loss and backward passes.
+//
+// Host arithmetic that feeds an order decision (camera centre and ground
+// axes of the perspective box cull) is done in binary32, one rounding per
+// operation, in the same order as the oracle; this file is compiled with
+// -ffp-contract=off so the host compiler cannot fuse it.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "kernels.h"
+
+using namespace rogs;
+
+struct rogs_ctx {
+    rogs_config cfg;
+    int device = 0;
+    std::string err;
+    // capacity-sized scratch
+    uint32_t *dk_a = nullptr, *dv_a = nullptr, *dk_b = nullptr, *dv_b = nullptr, *dk_c = nullptr, *dv_c = nullptr;
+    uint32_t *pk_a = nullptr, *pv_a = nullptr, *pk_b = nullptr, *pk_c = nullptr, *pv_c = nullptr;
+    uint32_t* hist = nullptr;
+    unsigned long long *pair_off = nullptr, *pair_tiles = nullptr;
+    float* rec_grad = nullptr;
+    // grown on demand
+    uint32_t *bits = nullptr, *word_off = nullptr, *bits_tiles = nullptr;
+    size_t bits_cap = 0;  // words
+    float* loss_partials = nullptr;
+    unsigned long long* loss_counter = nullptr;
+    size_t loss_cap = 0;  // blocks
+    ViewParams* loss_views = nullptr;
+    float* poses = nullptr;
+    size_t poses_cap = 0;  // floats
+};
+
+namespace {
+
+rogs_status fail(rogs_ctx* ctx, rogs_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+#define ROGS_CUDA(ctx, expr)                                                                        \
+    do {                                                                                            \
+        cudaError_t e_ = (expr);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(ctx, ROGS_ERR_CUDA, std::string(#expr ": ") + cudaGetErrorString(e_));      \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+template <class T>
+rogs_status grow(rogs_ctx* ctx, T*& ptr, size_t& cap, size_t need, cudaStream_t s, bool zero = false) {
+    if (need <= cap && ptr) return ROGS_OK;
+    if (capturing(s))
+        return fail(ctx, ROGS_ERR_CAPACITY, "scratch must grow during stream capture; call rogs_reserve first");
+    if (ptr) {
+        cudaStreamSynchronize(s);
+        cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+    }
+    size_t n = need > 0 ? need : 1;
+    cudaError_t e = cudaMalloc((void**)&ptr, n * sizeof(T));
+    if (e != cudaSuccess) return fail(ctx, ROGS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    if (zero) cudaMemset(ptr, 0, n * sizeof(T));
+    cap = n;
+    return ROGS_OK;
+}
+
+Consts make_consts(const rogs_config& c) {
+    Consts k;
+    k.t_min = c.t_min;
+    k.alpha_min = c.alpha_min;
+    k.alpha_max = c.alpha_max;
+    k.eps = c.eps_dilate;
+    k.near_plane = c.near_plane;
+    k.box_half_x = c.box_half_x;
+    k.box_depth = c.box_depth;
+    k.tile_w = c.tile_w;
+    k.tile_h = c.tile_h;
+    k.C = c.num_classes;
+    return k;
+}
+
+// Derive device view parameters; returns false with a message on bad input.
+bool make_views(const rogs_config& cfg, const rogs_camera* cams, int n, ViewsArg& va, long long& total_tiles,
+                long long& total_pix, std::string& err) {
+    total_tiles = 0;
+    total_pix = 0;
+    for (int i = 0; i < n; ++i) {
+        const rogs_camera& c = cams[i];
+        ViewParams& v = va.v[i];
+        std::memset(&v, 0, sizeof(v));
+        if (c.kind != ROGS_PERSP && c.kind != ROGS_ORTHO) { err = "camera kind must be ROGS_PERSP or ROGS_ORTHO"; return false; }
+        if (c.width <= 0 || c.height <= 0) { err = "camera width and height must be positive"; return false; }
+        if (!(c.fx > 0.0f) || !(c.fy > 0.0f) || !std::isfinite(c.fx) || !std::isfinite(c.fy)) {
+            err = "camera focal lengths must be positive and finite";
+            return false;
+        }
+        bool finite = std::isfinite(c.cx) && std::isfinite(c.cy);
+        for (int k = 0; k < 9; ++k) finite = finite && std::isfinite(c.R_wc[k]);
+        for (int k = 0; k < 3; ++k) finite = finite && std::isfinite(c.t_wc[k]);
+        if (!finite) { err = "camera parameters must be finite"; return false; }
+        v.kind = c.kind;
+        v.W = c.width;
+        v.H = c.height;
+        v.tiles_x = (c.width + cfg.tile_w - 1) / cfg.tile_w;
+        v.tiles_y = (c.height + cfg.tile_h - 1) / cfg.tile_h;
+        if (v.tiles_x > 65535 || v.tiles_y > 65535) { err = "camera too large for 16-bit tile coordinates"; return false; }
+        v.exp_idx = c.exposure_idx;
+        v.box = c.use_box_cull ? 1 : 0;
+        v.tile_base = total_tiles;
+        v.pix_base = total_pix;
+        total_tiles += (long long)v.tiles_x * v.tiles_y;
+        total_pix += (long long)c.width * c.height;
+        v.fx = c.fx; v.fy = c.fy; v.cx = c.cx; v.cy = c.cy;
+        for (int k = 0; k < 9; ++k) v.R[k] = c.R_wc[k];
+        for (int k = 0; k < 3; ++k) v.t[k] = c.t_wc[k];
+        // camera centre o = -R^T t (binary32, fixed order)
+        {
+            float a = c.R_wc[0] * c.t_wc[0];
+            float b = c.R_wc[3] * c.t_wc[1];
+            float s = a + b;
+            float d = c.R_wc[6] * c.t_wc[2];
+            s = s + d;
+            v.ox = -s;
+            a = c.R_wc[1] * c.t_wc[0];
+            b = c.R_wc[4] * c.t_wc[1];
+            s = a + b;
+            d = c.R_wc[7] * c.t_wc[2];
+            s = s + d;
+            v.oy = -s;
+        }
+        // ground-projected camera x and z axes, normalised (binary32)
+        {
+            float p = c.R_wc[0] * c.R_wc[0];
+            float q = c.R_wc[1] * c.R_wc[1];
+            float nx = std::sqrt(p + q);
+            p = c.R_wc[6] * c.R_wc[6];
+            q = c.R_wc[7] * c.R_wc[7];
+            float nz = std::sqrt(p + q);
+            v.box_ok = (nx >= 1e-6f && nz >= 1e-6f) ? 1 : 0;
+            if (v.box_ok) {
+                v.xh0 = c.R_wc[0] / nx; v.xh1 = c.R_wc[1] / nx;
+                v.zh0 = c.R_wc[6] / nz; v.zh1 = c.R_wc[7] / nz;
+            }
+        }
+        v.lim_x = (float)(cfg.jac_clamp * (0.5 * c.width / c.fx));
+        v.lim_y = (float)(cfg.jac_clamp * (0.5 * c.height / c.fy));
+    }
+    if (total_tiles >= (1ll << 32)) { err = "too many tiles in one call"; return false; }
+    return true;
+}
+
+struct Layout {
+    rogs_state_layout l;
+};
+
+rogs_state_layout layout_for(const rogs_config& cfg, long long total_tiles, long long total_pix) {
+    rogs_state_layout L;
+    size_t off = 0;
+    L.header = off; off = align256(off + sizeof(StateHeader));
+    L.views = off; off = align256(off + sizeof(ViewParams) * kMaxViews);
+    L.records = off; off = align256(off + sizeof(Record) * (size_t)cfg.record_capacity);
+    L.rects = off; off = align256(off + 8 * (size_t)cfg.record_capacity);
+    L.pair_rec = off; off = align256(off + 4 * (size_t)cfg.pair_capacity);
+    L.tile_range = off; off = align256(off + 8 * (size_t)total_tiles);
+    L.pix_T = off; off = align256(off + 4 * (size_t)total_pix);
+    L.pix_last = off; off = align256(off + 4 * (size_t)total_pix);
+    L.total_bytes = off;
+    L.total_tiles = total_tiles;
+    L.total_pixels = total_pix;
+    return L;
+}
+
+int bits_for(long long n) {
+    int b = 0;
+    while (b < 32 && (1ll << b) < n) ++b;
+    return b;
+}
+
+bool valid_config(const rogs_config& c, std::string& err) {
+    const bool tile_ok = (c.tile_w == 16 && c.tile_h == 16) || (c.tile_w == 32 && c.tile_h == 8) ||
+                         (c.tile_w == 8 && c.tile_h == 8);
+    if (!tile_ok) { err = "tile must be 16x16, 32x8 or 8x8"; return false; }
+    if (c.num_classes < 0 || c.num_classes > ROGS_MAX_CLASSES) { err = "num_classes out of range"; return false; }
+    if (c.record_capacity < 1 || c.record_capacity > 0xffffffffll) { err = "record_capacity out of range"; return false; }
+    if (c.pair_capacity < 1 || c.pair_capacity > 0xffffffffll) { err = "pair_capacity out of range"; return false; }
+    if (!(c.alpha_min > 0.0f) || !(c.alpha_max > c.alpha_min) || !(c.alpha_max < 1.0f)) {
+        err = "need 0 < alpha_min < alpha_max < 1";
+        return false;
+    }
+    if (!(c.t_min > 0.0f) || !(c.t_min < 1.0f)) { err = "need 0 < t_min < 1"; return false; }
+    if (!(c.eps_dilate >= 0.0f)) { err = "eps_dilate must be >= 0"; return false; }
+    return true;
+}
+
+bool check_surfels(const rogs_surfels* s, int C, std::string& err) {
+    if (!s) { err = "surfels is NULL"; return false; }
+    if (s->n < 0) { err = "negative surfel count"; return false; }
+    if (s->n == 0) return true;
+    if (!s->xyz || !s->scale || !s->quat || !s->opacity || !s->rgb || (C > 0 && !s->sem)) {
+        err = "a surfel attribute pointer is NULL";
+        return false;
+    }
+    if (((uintptr_t)s->quat & 15u) || ((uintptr_t)s->scale & 7u) || ((uintptr_t)s->xyz & 3u)) {
+        err = "quat must be 16-byte and scale 8-byte aligned";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+rogs_status rogs_default_config(int32_t num_classes, int64_t record_capacity, int64_t pair_capacity,
+                                rogs_config* cfg) {
+    if (!cfg) return ROGS_ERR_INVALID;
+    cfg->tile_w = 16;
+    cfg->tile_h = 16;
+    cfg->num_classes = num_classes;
+    cfg->t_min = 1e-4f;
+    cfg->alpha_min = 1.0f / 255.0f;
+    cfg->alpha_max = 0.99f;
+    cfg->eps_dilate = 0.3f;
+    cfg->near_plane = 0.2f;
+    cfg->box_half_x = 20.0f;
+    cfg->box_depth = 40.0f;
+    cfg->jac_clamp = 1.3f;
+    cfg->record_capacity = record_capacity;
+    cfg->pair_capacity = pair_capacity;
+    return ROGS_OK;
+}
+
+rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
+    if (!cfg || !out) return ROGS_ERR_INVALID;
+    *out = nullptr;
+    std::string err;
+    if (!valid_config(*cfg, err)) return ROGS_ERR_INVALID;
+    rogs_ctx* ctx = new rogs_ctx();
+    ctx->cfg = *cfg;
+    cudaGetDevice(&ctx->device);
+    const size_t R = (size_t)cfg->record_capacity, P = (size_t)cfg->pair_capacity;
+    const size_t big = R > P ? R : P;
+    size_t c0 = 0;
+    rogs_status st = ROGS_OK;
+#define ROGS_ALLOC(ptr, count)                                                      \
+    do {                                                                            \
+        size_t cap_ = 0;                                                            \
+        if (st == ROGS_OK) st = grow(ctx, ptr, cap_, (count), nullptr);             \
+    } while (0)
+    ROGS_ALLOC(ctx->dk_a, R); ROGS_ALLOC(ctx->dv_a, R); ROGS_ALLOC(ctx->dk_b, R);
+    ROGS_ALLOC(ctx->dv_b, R); ROGS_ALLOC(ctx->dk_c, R); ROGS_ALLOC(ctx->dv_c, R);
+    ROGS_ALLOC(ctx->pk_a, P); ROGS_ALLOC(ctx->pv_a, P); ROGS_ALLOC(ctx->pk_b, P);
+    ROGS_ALLOC(ctx->pk_c, P); ROGS_ALLOC(ctx->pv_c, P);
+    ROGS_ALLOC(ctx->hist, radix_hist_words(big));
+    ROGS_ALLOC(ctx->pair_off, R + 1);
+    ROGS_ALLOC(ctx->pair_tiles, scan_tile_sums_words(R));
+    if (st == ROGS_OK) {
+        size_t cap_ = 0;
+        st = grow(ctx, ctx->rec_grad, cap_, R * (size_t)grad_channels(cfg->num_classes), nullptr, true);
+    }
+    ROGS_ALLOC(ctx->loss_views, (size_t)kMaxViews);
+#undef ROGS_ALLOC
+    (void)c0;
+    if (st != ROGS_OK) {
+        rogs_destroy(ctx);
+        return st;
+    }
+    cudaDeviceSynchronize();
+    *out = ctx;
+    return ROGS_OK;
+}
+
+void rogs_destroy(rogs_ctx* ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    void* ptrs[] = {ctx->dk_a, ctx->dv_a, ctx->dk_b, ctx->dv_b, ctx->dk_c, ctx->dv_c, ctx->pk_a, ctx->pv_a,
+                    ctx->pk_b, ctx->pk_c, ctx->pv_c, ctx->hist, ctx->pair_off, ctx->pair_tiles, ctx->rec_grad,
+                    ctx->bits, ctx->word_off, ctx->bits_tiles, ctx->loss_partials, ctx->loss_counter,
+                    ctx->loss_views, ctx->poses};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete ctx;
+}
+
+const char* rogs_last_error(const rogs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static rogs_status ensure_bits(rogs_ctx* ctx, long long n, int n_views, cudaStream_t s) {
+    const long long n_words = (n + 31) / 32;
+    const size_t need = (size_t)n_words * (size_t)n_views;
+    size_t c1 = ctx->bits_cap, c2 = ctx->bits_cap;
+    if (need <= ctx->bits_cap && ctx->bits) return ROGS_OK;
+    size_t c3 = 0;
+    rogs_status st = grow(ctx, ctx->bits, c1, need, s);
+    if (st == ROGS_OK) st = grow(ctx, ctx->word_off, c2, need, s);
+    if (st == ROGS_OK) {
+        if (ctx->bits_tiles) { cudaFree(ctx->bits_tiles); ctx->bits_tiles = nullptr; }
+        st = grow(ctx, ctx->bits_tiles, c3, scan_tile_sums_words(need), s);
+    }
+    if (st == ROGS_OK) ctx->bits_cap = c1 < c2 ? c1 : c2;
+    return st;
+}
+
+static rogs_status ensure_loss(rogs_ctx* ctx, long long total_pix, cudaStream_t s) {
+    const size_t nb = (size_t)loss_blocks(total_pix) + 1;
+    if (nb <= ctx->loss_cap && ctx->loss_partials) return ROGS_OK;
+    size_t c = ctx->loss_cap, c2 = 0;
+    rogs_status st = grow(ctx, ctx->loss_partials, c, nb, s);
+    if (st == ROGS_OK && !ctx->loss_counter) st = grow(ctx, ctx->loss_counter, c2, 1, s);
+    if (st == ROGS_OK) ctx->loss_cap = c;
+    return st;
+}
+
+rogs_status rogs_reserve(rogs_ctx* ctx, int64_t n_surfels, int32_t n_views) {
+    if (!ctx || n_surfels < 0 || n_views < 1 || n_views > kMaxViews) return fail(ctx, ROGS_ERR_INVALID, "bad reserve");
+    return ensure_bits(ctx, n_surfels, n_views, nullptr);
+}
+
+rogs_status rogs_state_layout_of(const rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views,
+                                 rogs_state_layout* layout, uint64_t* out_elems) {
+    if (!ctx || !cams || !layout || n_views < 1 || n_views > kMaxViews) return ROGS_ERR_INVALID;
+    static thread_local ViewsArg va;
+    long long tt, tp;
+    std::string err;
+    if (!make_views(ctx->cfg, cams, n_views, va, tt, tp, err)) {
+        const_cast<rogs_ctx*>(ctx)->err = err;
+        return ROGS_ERR_INVALID;
+    }
+    *layout = layout_for(ctx->cfg, tt, tp);
+    if (out_elems) *out_elems = (uint64_t)(3 + ctx->cfg.num_classes + 1) * (uint64_t)tp;
+    return ROGS_OK;
+}
+
+rogs_status rogs_state_counts(rogs_ctx* ctx, const void* state, rogs_counts* counts, rogs_stream stream) {
+    if (!ctx || !state || !counts) return fail(ctx, ROGS_ERR_INVALID, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    ROGS_CUDA(ctx, cudaMemcpyAsync(counts, state, sizeof(rogs_counts), cudaMemcpyDeviceToHost, s));
+    ROGS_CUDA(ctx, cudaStreamSynchronize(s));
+    if (counts->status) {
+        char buf[256];
+        std::snprintf(buf, sizeof(buf), "capacity exceeded: need %llu records (cap %lld), %llu pairs (cap %lld)",
+                      (unsigned long long)counts->need_records, (long long)ctx->cfg.record_capacity,
+                      (unsigned long long)counts->need_pairs, (long long)ctx->cfg.pair_capacity);
+        return fail(ctx, ROGS_ERR_CAPACITY, buf);
+    }
+    return ROGS_OK;
+}
+
+rogs_status rogs_init_from_poses(rogs_ctx* ctx, const float* grid_xy, int64_t n, const float* poses, int64_t n_poses,
+                                 int32_t exact_plane, float* out_z, float* out_quat, int32_t* out_nearest,
+                                 rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    if (n < 0 || n_poses < 1 || !poses) return fail(ctx, ROGS_ERR_INVALID, "need n >= 0 and at least one pose");
+    if (n > 0 && (!grid_xy || !out_z || !out_quat)) return fail(ctx, ROGS_ERR_INVALID, "null device pointer");
+    if (((uintptr_t)out_quat & 15u) || ((uintptr_t)grid_xy & 7u))
+        return fail(ctx, ROGS_ERR_INVALID, "out_quat must be 16-byte and grid_xy 8-byte aligned");
+    for (int64_t v = 0; v < n_poses; ++v) {
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(poses[12 * v + k])) return fail(ctx, ROGS_ERR_INVALID, "pose values must be finite");
+        if (exact_plane && std::fabs(poses[12 * v + 3 + 8]) < 1e-6f)
+            return fail(ctx, ROGS_ERR_INVALID, "pose with |n33| < 1e-6 (road normal parallel to the ground)");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rogs_status st = grow(ctx, ctx->poses, ctx->poses_cap, (size_t)(12 * n_poses), s);
+    if (st != ROGS_OK) return st;
+    ROGS_CUDA(ctx, cudaMemcpyAsync(ctx->poses, poses, sizeof(float) * 12 * (size_t)n_poses, cudaMemcpyHostToDevice, s));
+    init_from_poses(grid_xy, n, ctx->poses, n_poses, exact_plane, out_z, out_quat, out_nearest, s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    ROGS_CUDA(ctx, cudaStreamSynchronize(s));
+    return ROGS_OK;
+}
+
+rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                            const float* exposure_ab, int32_t n_exposure, float* out, void* state,
+                            rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    const rogs_config& cfg = ctx->cfg;
+    std::string err;
+    if (!cams || n_views < 1 || n_views > kMaxViews) return fail(ctx, ROGS_ERR_INVALID, "n_views out of range");
+    if (!check_surfels(surfels, cfg.num_classes, err)) return fail(ctx, ROGS_ERR_INVALID, err);
+    if (!out || !state || !exposure_ab || n_exposure < 1) return fail(ctx, ROGS_ERR_INVALID, "null output/state/exposure");
+    if ((uintptr_t)state & 255u) return fail(ctx, ROGS_ERR_INVALID, "state must be 256-byte aligned");
+    if ((unsigned long long)surfels->n * (unsigned long long)n_views >= 0xffffffffull)
+        return fail(ctx, ROGS_ERR_INVALID, "surfels x views must be < 2^32");
+    static thread_local ViewsArg va;
+    long long total_tiles, total_pix;
+    if (!make_views(cfg, cams, n_views, va, total_tiles, total_pix, err)) return fail(ctx, ROGS_ERR_INVALID, err);
+    for (int i = 0; i < n_views; ++i)
+        if (cams[i].exposure_idx < 0 || cams[i].exposure_idx >= n_exposure)
+            return fail(ctx, ROGS_ERR_INVALID, "exposure_idx out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = surfels->n;
+    const long long n_words = (n + 31) / 32;
+    rogs_status st = ensure_bits(ctx, n, n_views, s);
+    if (st != ROGS_OK) return st;
+
+    const rogs_state_layout L = layout_for(cfg, total_tiles, total_pix);
+    char* sb = (char*)state;
+    StateHeader* hdr = (StateHeader*)(sb + L.header);
+    ViewParams* views = (ViewParams*)(sb + L.views);
+    Record* recs = (Record*)(sb + L.records);
+    uint2* rects = (uint2*)(sb + L.rects);
+    uint32_t* pair_rec = (uint32_t*)(sb + L.pair_rec);
+    uint2* ranges = (uint2*)(sb + L.tile_range);
+    float* pix_T = (float*)(sb + L.pix_T);
+    uint32_t* pix_last = (uint32_t*)(sb + L.pix_last);
+    const unsigned long long rcap = (unsigned long long)cfg.record_capacity;
+    const unsigned long long pcap = (unsigned long long)cfg.pair_capacity;
+    const Consts k = make_consts(cfg);
+    const SurfelPtrs sp{surfels->xyz, surfels->scale, surfels->quat, surfels->opacity, surfels->rgb, surfels->sem, n};
+
+    upload_views(va, n_views, views, hdr, s);
+    if (n > 0) {
+        cull_views(views, n_views, k, sp, ctx->bits, n_words, s);
+        scan_visible(ctx->bits, n_words * n_views, ctx->word_off, ctx->bits_tiles, hdr, rcap, s);
+        project_records(views, n_views, k, sp, ctx->bits, ctx->word_off, n_words, recs, rects, ctx->dk_a, ctx->dv_a,
+                        rcap, s);
+        // depth sort: stable on the binary32 depth key; ties keep (view, surfel) order
+        radix_sort_pairs(ctx->dk_a, ctx->dv_a, ctx->dk_b, ctx->dv_b, ctx->dk_c, ctx->dv_c, &hdr->n_records, rcap, 32,
+                         ctx->hist, s);
+        scan_pairs(ctx->dv_b, rects, hdr, rcap, ctx->pair_off, ctx->pair_tiles, hdr, pcap, s);
+        emit_pairs(views, ctx->dv_b, recs, rects, ctx->pair_off, hdr, rcap, ctx->pk_a, ctx->pv_a, pcap, s);
+        // tile sort: stable on the global tile id; lists stay in depth order
+        radix_sort_pairs(ctx->pk_a, ctx->pv_a, ctx->pk_b, pair_rec, ctx->pk_c, ctx->pv_c, &hdr->n_pairs, pcap,
+                         bits_for(total_tiles), ctx->hist, s);
+    }
+    ROGS_CUDA(ctx, cudaMemsetAsync(ranges, 0, 8 * (size_t)total_tiles, s));
+    if (n > 0) tile_ranges(ctx->pk_b, hdr, pcap, ranges, s);
+    composite_fwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
+                  exposure_ab, out, pix_T, pix_last, hdr, s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+rogs_status rogs_loss(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, const float* out, const float* tgt_rgb,
+                      const int32_t* label, const uint8_t* mask, float lambda_c, float lambda_s, float* loss,
+                      float* grad_out, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    if (!cams || n_views < 1 || n_views > kMaxViews) return fail(ctx, ROGS_ERR_INVALID, "n_views out of range");
+    if (!out || !tgt_rgb || !mask || !loss || !grad_out || (ctx->cfg.num_classes > 0 && !label))
+        return fail(ctx, ROGS_ERR_INVALID, "null device pointer");
+    static thread_local ViewsArg va;
+    long long tt, tp;
+    std::string err;
+    if (!make_views(ctx->cfg, cams, n_views, va, tt, tp, err)) return fail(ctx, ROGS_ERR_INVALID, err);
+    cudaStream_t s = (cudaStream_t)stream;
+    rogs_status st = ensure_loss(ctx, tp, s);
+    if (st != ROGS_OK) return st;
+    upload_views(va, n_views, ctx->loss_views, nullptr, s);
+    loss_fwd_bwd(ctx->loss_views, n_views, tp, ctx->cfg.num_classes, out, tgt_rgb, label, mask, lambda_c, lambda_s,
+                 loss, grad_out, ctx->loss_counter, ctx->loss_partials, (int)ctx->loss_cap, s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                            const float* exposure_ab, int32_t n_exposure, const void* state, const float* grad_out,
+                            const rogs_grads* grads, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    const rogs_config& cfg = ctx->cfg;
+    std::string err;
+    if (!cams || n_views < 1 || n_views > kMaxViews) return fail(ctx, ROGS_ERR_INVALID, "n_views out of range");
+    if (!check_surfels(surfels, cfg.num_classes, err)) return fail(ctx, ROGS_ERR_INVALID, err);
+    if (!state || !grad_out || !grads || !exposure_ab || n_exposure < 1)
+        return fail(ctx, ROGS_ERR_INVALID, "null state/grad_out/grads/exposure");
+    if ((uintptr_t)state & 255u) return fail(ctx, ROGS_ERR_INVALID, "state must be 256-byte aligned");
+    static thread_local ViewsArg va;
+    long long total_tiles, total_pix;
+    if (!make_views(cfg, cams, n_views, va, total_tiles, total_pix, err)) return fail(ctx, ROGS_ERR_INVALID, err);
+    for (int i = 0; i < n_views; ++i)
+        if (cams[i].exposure_idx < 0 || cams[i].exposure_idx >= n_exposure)
+            return fail(ctx, ROGS_ERR_INVALID, "exposure_idx out of range");
+    if (grads->quat && ((uintptr_t)grads->quat & 15u)) return fail(ctx, ROGS_ERR_INVALID, "grad quat alignment");
+    cudaStream_t s = (cudaStream_t)stream;
+    const rogs_state_layout L = layout_for(cfg, total_tiles, total_pix);
+    const char* sb = (const char*)state;
+    const StateHeader* hdr = (const StateHeader*)(sb + L.header);
+    const ViewParams* views = (const ViewParams*)(sb + L.views);
+    const Record* recs = (const Record*)(sb + L.records);
+    const uint32_t* pair_rec = (const uint32_t*)(sb + L.pair_rec);
+    const uint2* ranges = (const uint2*)(sb + L.tile_range);
+    const float* pix_T = (const float*)(sb + L.pix_T);
+    const uint32_t* pix_last = (const uint32_t*)(sb + L.pix_last);
+    const Consts k = make_consts(cfg);
+    const SurfelPtrs sp{surfels->xyz, surfels->scale, surfels->quat, surfels->opacity, surfels->rgb, surfels->sem,
+                        surfels->n};
+    const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
+    composite_bwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
+                  exposure_ab, grad_out, pix_T, pix_last, ctx->rec_grad, grads->exposure, s);
+    project_bwd(views, k, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp,
+                s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
+                            int32_t key_bits, uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    if (n < 0 || n > ctx->cfg.pair_capacity) return fail(ctx, ROGS_ERR_INVALID, "n outside [0, pair_capacity]");
+    if (key_bits < 0 || key_bits > 32) return fail(ctx, ROGS_ERR_INVALID, "key_bits outside [0, 32]");
+    if (n == 0) return ROGS_OK;
+    if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(ctx, ROGS_ERR_INVALID, "null device pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, ctx->pk_c, ctx->pv_c, nullptr, (unsigned long long)n,
+                     key_bits, ctx->hist, s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+}  // extern "C"

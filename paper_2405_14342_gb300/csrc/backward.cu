@@ -1,0 +1,434 @@
+// backward.cu -- stage 4: reverse-order backward of the compositing and the
+// projection (the adjoint of RoGs Eqs. 2, 5, 6, 7; not written in the paper).
+//
+// composite_bwd_k: one CTA per tile.  Each pixel starts from its final
+// transmittance T and walks its tile list backwards from its last composited
+// entry, recovering T_k = T_{k+1} / (1 - a_k) and carrying the suffix sum
+// S_k = sum_{j>k} w_j f_j, so that
+//     dout/df_k = w_k,   dout/da_k = T_k f_k - S_k / (1 - a_k)
+// need no per-pixel list.  The chunk of entries is re-staged in shared memory
+// exactly as in the forward and a_k is recomputed with the same function, so
+// the same entries contribute.  Each warp reduces an entry's gradient vector
+// (mean 2, conic 3, alpha 1, features 3 + C + 1) across its 32 pixels with a
+// transposing butterfly (31 shuffles leave lane c holding the warp sum of
+// channel c), adds it into a per-chunk shared-memory accumulator, and the CTA
+// flushes the chunk with one global atomic per non-zero (entry, channel).
+//
+// project_bwd_k: one thread per record; chains the 2D gradients through the
+// conic inverse, Sigma' = T2 T2^T + eps I, T2 = J W M, the perspective
+// Jacobian and mean, the quaternion normalisation and M = R[:, :2] diag(s),
+// and adds the per-surfel results (several views touch one surfel) with
+// atomics.  It clears each record's gradient row after reading it, so the
+// buffer is all zero again for the next backward.
+#include "kernels.h"
+
+namespace rogs {
+
+int grad_channels(int C) { return padded_channels(C) <= 24 ? 32 : 64; }
+
+template <int NCP>
+__device__ __forceinline__ void stage_entry_bwd(const Record* __restrict__ recs, const uint32_t rec,
+                                                const SurfelPtrs& sp, int C, float4* s_m, float4* s_c, float* s_f,
+                                                uint32_t* s_rec, int slot) {
+    const float4* r4 = reinterpret_cast<const float4*>(recs + rec);
+    const float4 a = r4[0];
+    const float4 b = r4[1];
+    const float4 c = r4[2];
+    s_m[slot] = a;
+    s_c[slot] = b;
+    s_rec[slot] = rec;
+    const uint32_t s = __float_as_uint(c.z);
+    float* f = s_f + slot * NCP;
+    f[0] = sp.rgb[3ull * s];
+    f[1] = sp.rgb[3ull * s + 1];
+    f[2] = sp.rgb[3ull * s + 2];
+    const float* sem = sp.sem + (unsigned long long)C * s;
+    for (int ch = 0; ch < C; ++ch) f[3 + ch] = sem[ch];
+    f[3 + C] = c.x;
+#pragma unroll
+    for (int ch = 0; ch < NCP; ++ch)
+        if (ch > 3 + C) f[ch] = 0.0f;
+}
+
+// Transposing butterfly over 32 values: on return v[0] of lane l holds the
+// sum over the warp of every lane's v[l].
+__device__ __forceinline__ void transpose_reduce32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(kFull, send, h);
+        }
+    }
+}
+
+template <int TW, int TH, int NCP, int GP>
+__global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __restrict__ views, int n_views, Consts k,
+                                                           SurfelPtrs sp, const Record* __restrict__ recs,
+                                                           const uint32_t* __restrict__ pair_rec,
+                                                           const uint2* __restrict__ ranges,
+                                                           const float* __restrict__ exposure_ab,
+                                                           const float* __restrict__ grad_out,
+                                                           const float* __restrict__ pix_T,
+                                                           const uint32_t* __restrict__ pix_last,
+                                                           float* __restrict__ rec_grad, float* __restrict__ d_exposure) {
+    constexpr int BLK = TW * TH;
+    constexpr int WX = TW / 8;
+    constexpr int NW = BLK / 32;
+    extern __shared__ float4 smem_bwd[];
+    float4* s_m = smem_bwd;
+    float4* s_c = s_m + BLK;
+    float* s_f = reinterpret_cast<float*>(s_c + BLK);
+    float* s_g = s_f + BLK * NCP;
+    uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_g + BLK * GP);
+    __shared__ uint32_t s_maxlast;
+    __shared__ float s_exp[NW][2];
+
+    const long long tile = blockIdx.x;
+    const int vi = view_of_tile(views, n_views, tile);
+    const ViewParams& v = views[vi];
+    const int W = v.W, H = v.H;
+    const long long lt = tile - v.tile_base;
+    const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = tx * TW + (warp % WX) * 8 + (lane & 7);
+    const int py = ty * TH + (warp / WX) * 4 + (lane >> 3);
+    const bool inside = px < W && py < H;
+    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const uint2 rg = ranges[tile];
+    const uint32_t start = rg.x;
+    const int C = k.C;
+    const int nch = 3 + C + 1;
+    const float amin = k.alpha_min, amax = k.alpha_max;
+    const float ea = expf(exposure_ab[2 * v.exp_idx]);
+
+    float T = 1.0f;
+    uint32_t last = 0;
+    float G[NCP], S[NCP];
+#pragma unroll
+    for (int ch = 0; ch < NCP; ++ch) { G[ch] = 0.0f; S[ch] = 0.0f; }
+    float gsum_rgb = 0.0f;
+    if (inside) {
+        const long long pix = v.pix_base + (long long)py * W + px;
+        const long long plane = (long long)W * H;
+        const float* go = grad_out + (long long)nch * v.pix_base + (long long)py * W + px;
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch)
+            if (ch < nch) G[ch] = go[ch * plane];
+        gsum_rgb = G[0] + G[1] + G[2];
+        G[0] *= ea; G[1] *= ea; G[2] *= ea;   // through c' = e^a c + b
+        T = pix_T[pix];
+        last = pix_last[pix];
+    }
+    if (threadIdx.x == 0) s_maxlast = 0;
+    __syncthreads();
+    if (last) atomicMax(&s_maxlast, last);
+    __syncthreads();
+    const uint32_t maxlast = s_maxlast;
+
+    for (uint32_t cend = maxlast; cend > 0;) {
+        const uint32_t cbeg = cend > (uint32_t)BLK ? cend - BLK : 0u;
+        const int cnt = (int)(cend - cbeg);
+        if (threadIdx.x < cnt)
+            stage_entry_bwd<NCP>(recs, pair_rec[start + cbeg + threadIdx.x], sp, C, s_m, s_c, s_f, s_rec, threadIdx.x);
+        for (int q = threadIdx.x; q < cnt * GP; q += BLK) s_g[q] = 0.0f;
+        __syncthreads();
+        for (int jj = cnt - 1; jj >= 0; --jj) {
+            const uint32_t jl = cbeg + (uint32_t)jj;  // index in the tile list
+            float gv[GP];
+#pragma unroll
+            for (int q = 0; q < GP; ++q) gv[q] = 0.0f;
+            bool contrib = false;
+            if (jl < last) {
+                const float4 m = s_m[jj];
+                const float4 c = s_c[jj];
+                const float dx = pix_offset(pxc, m.x, m.z);
+                const float dy = pix_offset(pyc, m.y, m.w);
+                float g;
+                const float a = surfel_alpha(dx, dy, c.x, c.y, c.z, c.w, amax, g);
+                if (a >= amin) {
+                    contrib = true;
+                    const float oma = __fsub_rn(1.0f, a);
+                    T = __fdiv_rn(T, oma);           // T_k
+                    const float w = a * T;
+                    const float ioma = 1.0f / oma;
+                    const float* f = s_f + jj * NCP;
+                    float da = 0.0f;
+#pragma unroll
+                    for (int ch = 0; ch < NCP; ++ch) {
+                        const float fc = f[ch];
+                        if (6 + ch < GP) gv[6 + ch] = w * G[ch];
+                        da = fmaf(G[ch], fmaf(T, fc, -S[ch] * ioma), da);
+                        S[ch] = fmaf(w, fc, S[ch]);
+                    }
+                    const float ag = c.w * g;
+                    if (ag < amax) {
+                        const float dpow = da * ag;
+                        gv[0] = dpow * (c.x * dx + c.y * dy);
+                        gv[1] = dpow * (c.y * dx + c.z * dy);
+                        gv[2] = -0.5f * dpow * dx * dx;
+                        gv[3] = -dpow * dx * dy;
+                        gv[4] = -0.5f * dpow * dy * dy;
+                        gv[5] = da * g;
+                    }
+                }
+            }
+            if (__any_sync(kFull, contrib)) {
+                if (GP == 32) {
+                    float r[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) r[q] = gv[q];
+                    transpose_reduce32(r, lane);
+                    if (r[0] != 0.0f) atomicAdd(&s_g[jj * GP + lane], r[0]);
+                } else {
+                    float r[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) r[q] = gv[q];
+                    transpose_reduce32(r, lane);
+                    if (r[0] != 0.0f) atomicAdd(&s_g[jj * GP + lane], r[0]);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) r[q] = gv[(32 + q) % GP];
+                    transpose_reduce32(r, lane);
+                    if (r[0] != 0.0f) atomicAdd(&s_g[jj * GP + 32 + lane], r[0]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt * GP; q += BLK) {
+            const float val = s_g[q];
+            if (val != 0.0f) atomicAdd(&rec_grad[(unsigned long long)s_rec[q / GP] * GP + (q % GP)], val);
+        }
+        __syncthreads();
+        cend = cbeg;
+    }
+
+    // exposure (Eq. 7): dL/db = sum g', dL/da = sum g' e^a c_raw, c_raw = S_rgb
+    float e_a = 0.0f, e_b = 0.0f;
+    if (inside) {
+        e_b = gsum_rgb;
+        // G[0..2] already hold e^a g'; c_raw = S[0..2]
+        e_a = G[0] * S[0] + G[1] * S[1] + G[2] * S[2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e_a += __shfl_xor_sync(kFull, e_a, o);
+        e_b += __shfl_xor_sync(kFull, e_b, o);
+    }
+    if (lane == 0) { s_exp[warp][0] = e_a; s_exp[warp][1] = e_b; }
+    __syncthreads();
+    if (threadIdx.x == 0 && d_exposure) {
+        float ta = 0.0f, tb = 0.0f;
+        for (int w = 0; w < NW; ++w) { ta += s_exp[w][0]; tb += s_exp[w][1]; }
+        if (ta != 0.0f) atomicAdd(&d_exposure[2 * v.exp_idx], ta);
+        if (tb != 0.0f) atomicAdd(&d_exposure[2 * v.exp_idx + 1], tb);
+    }
+}
+
+static size_t bwd_smem_bytes(int blk, int ncp, int gp) {
+    return (size_t)blk * (32 + 4 * (size_t)ncp + 4 * (size_t)gp + 4);
+}
+
+template <int TW, int TH>
+static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
+                            Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
+                            const float* exposure_ab, const float* grad_out, const float* pix_T,
+                            const uint32_t* pix_last, float* rec_grad, float* d_exposure) {
+    dim3 grid((unsigned)total_tiles);
+#define ROGS_BWD(NCP, GP)                                                                                        \
+    do {                                                                                                         \
+        const size_t sm = bwd_smem_bytes(TW * TH, NCP, GP);                                                      \
+        static bool attr_set = false;                                                                            \
+        if (!attr_set) {                                                                                         \
+            cudaFuncSetAttribute(composite_bwd_k<TW, TH, NCP, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)sm);                                                                       \
+            attr_set = true;                                                                                     \
+        }                                                                                                        \
+        composite_bwd_k<TW, TH, NCP, GP><<<grid, TW * TH, sm, s>>>(views, n_views, k, sp, recs, pair_rec,        \
+                                                                   ranges, exposure_ab, grad_out, pix_T,         \
+                                                                   pix_last, rec_grad, d_exposure);              \
+    } while (0)
+    switch (ncp) {
+        case 8: ROGS_BWD(8, 32); break;
+        case 12: ROGS_BWD(12, 32); break;
+        case 16: ROGS_BWD(16, 32); break;
+        case 24: ROGS_BWD(24, 32); break;
+        case 32: ROGS_BWD(32, 64); break;
+        default: ROGS_BWD(64, 64); break;
+    }
+#undef ROGS_BWD
+}
+
+void composite_bwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
+                   Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
+                   const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,
+                   float* rec_grad, float* d_exposure, cudaStream_t s) {
+    const int ncp = padded_channels(C);
+    if (tile_w == 32 && tile_h == 8)
+        launch_bwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab,
+                               grad_out, pix_T, pix_last, rec_grad, d_exposure);
+    else if (tile_w == 8 && tile_h == 8)
+        launch_bwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab,
+                              grad_out, pix_T, pix_last, rec_grad, d_exposure);
+    else
+        launch_bwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab,
+                                grad_out, pix_T, pix_last, rec_grad, d_exposure);
+}
+
+// ----------------------------------------------------------- project_bwd
+
+__global__ void __launch_bounds__(256) project_bwd_k(const ViewParams* __restrict__ views, Consts k, SurfelPtrs sp,
+                                                     const Record* __restrict__ recs,
+                                                     const StateHeader* __restrict__ hdr, unsigned long long rec_cap,
+                                                     float* __restrict__ rec_grad, int C, int GP, GradPtrs gp) {
+    unsigned long long n = hdr->n_records;
+    if (n > rec_cap) n = rec_cap;
+    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < n;
+         r += (unsigned long long)gridDim.x * blockDim.x) {
+        float* gr = rec_grad + r * (unsigned long long)GP;
+        const int used = 6 + 3 + C + 1;
+        bool any = false;
+        float g6[6];
+        for (int q = 0; q < 6; ++q) { g6[q] = gr[q]; any |= g6[q] != 0.0f; }
+        const Record rec = recs[r];
+        const uint32_t i = rec.surfel;
+        // features: rgb, sem, depth
+        float dz_feat = 0.0f;
+        for (int q = 6; q < used; ++q) {
+            const float val = gr[q];
+            if (val == 0.0f) continue;
+            gr[q] = 0.0f;
+            const int ch = q - 6;
+            if (ch < 3) { if (gp.rgb) atomicAdd(&gp.rgb[3ull * i + ch], val); }
+            else if (ch < 3 + C) { if (gp.sem) atomicAdd(&gp.sem[(unsigned long long)C * i + (ch - 3)], val); }
+            else { dz_feat = val; any = true; }
+        }
+        for (int q = 0; q < 6; ++q) gr[q] = 0.0f;
+        if (!any) continue;
+        if (gp.opacity && g6[5] != 0.0f) atomicAdd(&gp.opacity[i], g6[5]);
+
+        const ViewParams& v = views[rec.view];
+        // recompute the forward quantities in FP32
+        const float x = sp.xyz[3ull * i], y = sp.xyz[3ull * i + 1], z = sp.xyz[3ull * i + 2];
+        float p[3];
+        for (int rr = 0; rr < 3; ++rr) {
+            df a = two_prod(v.R[3 * rr], x);
+            a = df_add(a, two_prod(v.R[3 * rr + 1], y));
+            a = df_add(a, two_prod(v.R[3 * rr + 2], z));
+            a = df_add_f(a, v.t[rr]);
+            p[rr] = __fadd_rn(a.hi, a.lo);
+        }
+        float J00, J02, J11, J12, uc = 0.0f, vc = 0.0f;
+        bool clx = false, cly = false;
+        const bool persp = v.kind == ROGS_PERSP;
+        if (persp) {
+            const float inv = 1.0f / p[2];
+            const float u = p[0] * inv, vv = p[1] * inv;
+            uc = fminf(fmaxf(u, -v.lim_x), v.lim_x);
+            vc = fminf(fmaxf(vv, -v.lim_y), v.lim_y);
+            clx = uc != u;
+            cly = vc != vv;
+            J00 = v.fx * inv; J02 = -v.fx * uc * inv; J11 = v.fy * inv; J12 = -v.fy * vc * inv;
+        } else {
+            J00 = v.fx; J02 = 0.0f; J11 = v.fy; J12 = 0.0f;
+        }
+        const float4 q4 = reinterpret_cast<const float4*>(sp.quat)[i];
+        const float qnorm2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+        const float qinv = rsqrtf(qnorm2);
+        const float w = q4.x * qinv, qx = q4.y * qinv, qy = q4.z * qinv, qz = q4.w * qinv;
+        const float2 s = reinterpret_cast<const float2*>(sp.scale)[i];
+        // R(q) columns 0, 1
+        const float R00 = 1.0f - 2.0f * (qy * qy + qz * qz), R10 = 2.0f * (qx * qy + w * qz), R20 = 2.0f * (qx * qz - w * qy);
+        const float R01 = 2.0f * (qx * qy - w * qz), R11 = 1.0f - 2.0f * (qx * qx + qz * qz), R21 = 2.0f * (qy * qz + w * qx);
+        const float m0[3] = {R00 * s.x, R10 * s.x, R20 * s.x};
+        const float m1[3] = {R01 * s.y, R11 * s.y, R21 * s.y};
+        float V0[3], V1[3];
+        for (int rr = 0; rr < 3; ++rr) {
+            V0[rr] = v.R[3 * rr] * m0[0] + v.R[3 * rr + 1] * m0[1] + v.R[3 * rr + 2] * m0[2];
+            V1[rr] = v.R[3 * rr] * m1[0] + v.R[3 * rr + 1] * m1[1] + v.R[3 * rr + 2] * m1[2];
+        }
+        // T2 = J V (2x2): columns t0 = J V0, t1 = J V1
+        const float t00 = J00 * V0[0] + J02 * V0[2], t10 = J11 * V0[1] + J12 * V0[2];
+        const float t01 = J00 * V1[0] + J02 * V1[2], t11 = J11 * V1[1] + J12 * V1[2];
+        // conic Q (recomputed as in the forward record)
+        const float A = rec.ca, B = rec.cb, Cc = rec.cc;
+        // dL/dSigma = -Q dQ Q, dQ symmetric with the shared off-diagonal split
+        const float q00 = g6[2], q01 = 0.5f * g6[3], q11 = g6[4];
+        const float a00 = A * q00 + B * q01, a01 = A * q01 + B * q11;
+        const float a10 = B * q00 + Cc * q01, a11 = B * q01 + Cc * q11;
+        const float dS00 = -(a00 * A + a01 * B), dS01 = -(a00 * B + a01 * Cc), dS11 = -(a10 * B + a11 * Cc);
+        // Sigma = T2 T2^T -> dT2 = 2 dS T2
+        const float dT00 = 2.0f * (dS00 * t00 + dS01 * t10), dT01 = 2.0f * (dS00 * t01 + dS01 * t11);
+        const float dT10 = 2.0f * (dS01 * t00 + dS11 * t10), dT11 = 2.0f * (dS01 * t01 + dS11 * t11);
+        // T2 = J V: dJ = dT2 V^T, dV = J^T dT2
+        const float dJ00 = dT00 * V0[0] + dT01 * V1[0];
+        const float dJ02 = dT00 * V0[2] + dT01 * V1[2];
+        const float dJ11 = dT10 * V0[1] + dT11 * V1[1];
+        const float dJ12 = dT10 * V0[2] + dT11 * V1[2];
+        float dV0[3], dV1[3];
+        dV0[0] = J00 * dT00; dV0[1] = J11 * dT10; dV0[2] = J02 * dT00 + J12 * dT10;
+        dV1[0] = J00 * dT01; dV1[1] = J11 * dT11; dV1[2] = J02 * dT01 + J12 * dT11;
+        // V = W M -> dM = W^T dV
+        float dm0[3], dm1[3];
+        for (int cc = 0; cc < 3; ++cc) {
+            dm0[cc] = v.R[cc] * dV0[0] + v.R[3 + cc] * dV0[1] + v.R[6 + cc] * dV0[2];
+            dm1[cc] = v.R[cc] * dV1[0] + v.R[3 + cc] * dV1[1] + v.R[6 + cc] * dV1[2];
+        }
+        const float dsx = dm0[0] * R00 + dm0[1] * R10 + dm0[2] * R20;
+        const float dsy = dm1[0] * R01 + dm1[1] * R11 + dm1[2] * R21;
+        // dR entries (row-major) for columns 0, 1
+        const float dR0 = dm0[0] * s.x, dR3 = dm0[1] * s.x, dR6 = dm0[2] * s.x;
+        const float dR1 = dm1[0] * s.y, dR4 = dm1[1] * s.y, dR7 = dm1[2] * s.y;
+        // derivative of R(q) entries w.r.t. the unit quaternion (columns 0, 1 only)
+        const float dw = 2.0f * (qz * dR3 - qy * dR6 - qz * dR1 + qx * dR7);
+        const float dx_ = 2.0f * (qy * dR3 + qz * dR6 + qy * dR1 - 2.0f * qx * dR4 + w * dR7);
+        const float dy_ = 2.0f * (-2.0f * qy * dR0 + qx * dR3 - w * dR6 + qx * dR1 + qz * dR7);
+        const float dz_ = 2.0f * (-2.0f * qz * dR0 + w * dR3 + qx * dR6 - w * dR1 - 2.0f * qz * dR4 + qy * dR7);
+        const float dot = w * dw + qx * dx_ + qy * dy_ + qz * dz_;
+        const float invn = qinv;
+        // position
+        float dp0 = 0.0f, dp1 = 0.0f, dp2 = dz_feat;
+        if (persp) {
+            const float iz = 1.0f / p[2], iz2 = iz * iz;
+            dp0 += g6[0] * v.fx * iz;
+            dp1 += g6[1] * v.fy * iz;
+            dp2 += -g6[0] * v.fx * p[0] * iz2 - g6[1] * v.fy * p[1] * iz2;
+            dp2 += dJ00 * (-v.fx * iz2) + dJ11 * (-v.fy * iz2);
+            if (!clx) { dp0 += dJ02 * (-v.fx * iz2); dp2 += dJ02 * (2.0f * v.fx * p[0] * iz2 * iz); }
+            else { dp2 += dJ02 * (v.fx * uc * iz2); }
+            if (!cly) { dp1 += dJ12 * (-v.fy * iz2); dp2 += dJ12 * (2.0f * v.fy * p[1] * iz2 * iz); }
+            else { dp2 += dJ12 * (v.fy * vc * iz2); }
+        } else {
+            dp0 += g6[0] * v.fx;
+            dp1 += g6[1] * v.fy;
+        }
+        if (gp.xyz) {
+            for (int cc = 0; cc < 3; ++cc) {
+                const float val = v.R[cc] * dp0 + v.R[3 + cc] * dp1 + v.R[6 + cc] * dp2;
+                if (val != 0.0f) atomicAdd(&gp.xyz[3ull * i + cc], val);
+            }
+        }
+        if (gp.scale) {
+            if (dsx != 0.0f) atomicAdd(&gp.scale[2ull * i], dsx);
+            if (dsy != 0.0f) atomicAdd(&gp.scale[2ull * i + 1], dsy);
+        }
+        if (gp.quat) {
+            atomicAdd(&gp.quat[4ull * i + 0], (dw - w * dot) * invn);
+            atomicAdd(&gp.quat[4ull * i + 1], (dx_ - qx * dot) * invn);
+            atomicAdd(&gp.quat[4ull * i + 2], (dy_ - qy * dot) * invn);
+            atomicAdd(&gp.quat[4ull * i + 3], (dz_ - qz * dot) * invn);
+        }
+    }
+}
+
+void project_bwd(const ViewParams* views, Consts k, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
+                 unsigned long long rec_cap, float* rec_grad, int C, GradPtrs g, cudaStream_t s) {
+    unsigned long long blocks = (rec_cap + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    project_bwd_k<<<(int)blocks, 256, 0, s>>>(views, k, sp, recs, hdr, rec_cap, rec_grad, C, grad_channels(C), g);
+}
+
+}  // namespace rogs

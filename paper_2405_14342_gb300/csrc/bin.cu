@@ -1,0 +1,100 @@
+// bin.cu -- stage 2: tile binning of the depth-sorted records.
+//
+// RoGs Sec. 3.3.1 composites, at each pixel, the surfels covering it in
+// ascending order of original depth.  After the depth sort of the records
+// (stable, so equal depths keep (view, surfel) order), every record emits one
+// (global tile id, record id) pair per tile of its conservative footprint
+// rectangle, in depth order.  A stable radix sort on the tile id then leaves
+// each tile's list ordered by (depth, surfel index), and tile_ranges_k finds
+// each tile's [start, end).
+#include "kernels.h"
+#include "scan.cuh"
+
+namespace rogs {
+
+__device__ __forceinline__ unsigned long long rect_tiles(uint2 r) {
+    const int x0 = (int)(r.x & 0xffffu), y0 = (int)(r.x >> 16);
+    const int x1 = (int)(r.y & 0xffffu), y1 = (int)(r.y >> 16);
+    if (x1 < x0 || y1 < y0) return 0ull;
+    return (unsigned long long)(x1 - x0 + 1) * (unsigned long long)(y1 - y0 + 1);
+}
+
+struct RectTilesF {
+    const uint32_t* sorted_rec;
+    const uint2* rects;
+    __device__ unsigned long long operator()(unsigned long long j) const { return rect_tiles(rects[sorted_rec[j]]); }
+};
+
+__global__ void finalize_pairs_k(StateHeader* hdr, unsigned long long cap) {
+    unsigned long long need = hdr->need_pairs;
+    hdr->n_pairs = need < cap ? need : cap;
+    if (need > cap) hdr->status |= kStatusPairOverflow;
+}
+
+void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeader* hdr_n_records,
+                unsigned long long rec_cap, unsigned long long* pair_off, unsigned long long* tile_sums,
+                StateHeader* hdr, unsigned long long pair_cap, cudaStream_t s) {
+    device_exclusive_scan<RectTilesF, unsigned long long>(RectTilesF{sorted_rec, rects}, &hdr_n_records->n_records,
+                                                          rec_cap, tile_sums, pair_off, &hdr->need_pairs, s);
+    finalize_pairs_k<<<1, 1, 0, s>>>(hdr, pair_cap);
+}
+
+__global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict__ views,
+                                                    const uint32_t* __restrict__ sorted_rec,
+                                                    const Record* __restrict__ recs, const uint2* __restrict__ rects,
+                                                    const unsigned long long* __restrict__ pair_off,
+                                                    const StateHeader* __restrict__ hdr, unsigned long long rec_cap,
+                                                    uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals,
+                                                    unsigned long long pair_cap) {
+    const unsigned long long n = scan_len(&hdr->n_records, rec_cap);
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t rec = sorted_rec[j];
+        const uint2 r = rects[rec];
+        const int x0 = (int)(r.x & 0xffffu), y0 = (int)(r.x >> 16);
+        const int x1 = (int)(r.y & 0xffffu), y1 = (int)(r.y >> 16);
+        if (x1 < x0 || y1 < y0) continue;
+        const ViewParams& v = views[recs[rec].view];
+        unsigned long long p = pair_off[j];
+        const long long base = v.tile_base;
+        for (int ty = y0; ty <= y1; ++ty) {
+            for (int tx = x0; tx <= x1; ++tx, ++p) {
+                if (p >= pair_cap) return;  // overflow: recorded by finalize_pairs_k
+                pair_keys[p] = (uint32_t)(base + (long long)ty * v.tiles_x + tx);
+                pair_vals[p] = rec;
+            }
+        }
+    }
+}
+
+void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Record* recs, const uint2* rects,
+                const unsigned long long* pair_off, const StateHeader* hdr, unsigned long long rec_cap,
+                uint32_t* pair_keys, uint32_t* pair_vals, unsigned long long pair_cap, cudaStream_t s) {
+    unsigned long long blocks = (rec_cap + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    emit_pairs_k<<<(int)blocks, 256, 0, s>>>(views, sorted_rec, recs, rects, pair_off, hdr, rec_cap, pair_keys,
+                                              pair_vals, pair_cap);
+}
+
+__global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict__ keys,
+                                                     const StateHeader* __restrict__ hdr, unsigned long long cap,
+                                                     uint2* __restrict__ ranges) {
+    const unsigned long long n = scan_len(&hdr->n_pairs, cap);
+    for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
+         p += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t t = keys[p];
+        if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
+        if (p + 1 == n || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+    }
+}
+
+void tile_ranges(const uint32_t* sorted_tile, const StateHeader* hdr, unsigned long long pair_cap, uint2* ranges,
+                 cudaStream_t s) {
+    unsigned long long blocks = (pair_cap + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    tile_ranges_k<<<(int)blocks, 256, 0, s>>>(sorted_tile, hdr, pair_cap, ranges);
+}
+
+}  // namespace rogs

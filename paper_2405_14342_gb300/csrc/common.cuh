@@ -1,0 +1,174 @@
+// common.cuh -- device-side types and helpers shared by the librogs kernels.
+//
+// Numerics.  GB300 runs FP64 at a small fraction of its FP32 rate, so the
+// few quantities that need more than binary32 (the camera-space centre and
+// the projected mean of a surfel, which suffer cancellation when the map is
+// hundreds of metres wide) are carried as unevaluated float pairs
+// ("double-float": hi + lo, error-free transforms built from fused
+// multiply-add, Dekker/Knuth two-sum and two-product).  The projected mean is
+// then stored as an integer pixel part plus a fraction in [0, 1), so that the
+// per-pixel offset (u + 0.5 - mean) is exact up to one rounding.
+//
+// Order decisions (binary32 depth sort key, near plane, perspective box cull)
+// use a fixed sequence of IEEE binary32 operations written with __fmul_rn /
+// __fadd_rn, which the compiler may not contract; the CPU oracle takes the
+// same decisions with the same operations.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rogs.h"
+
+namespace rogs {
+
+constexpr int kMaxViews = ROGS_MAX_VIEWS;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Per-view parameters, derived on the host from rogs_camera.
+struct ViewParams {
+    int kind, W, H, tiles_x, tiles_y, exp_idx, box, box_ok;
+    long long tile_base;  // global id of this view's first tile
+    long long pix_base;   // global index of this view's first pixel
+    float fx, fy, cx, cy;
+    float R[9], t[3];
+    float ox, oy, xh0, xh1, zh0, zh1;  // box cull helpers (binary32, fixed order)
+    float lim_x, lim_y;                // Jacobian clamp on x/z, y/z
+};
+
+struct ViewsArg {
+    ViewParams v[kMaxViews];
+};
+
+struct Consts {
+    float t_min, alpha_min, alpha_max, eps, near_plane, box_half_x, box_depth;
+    int tile_w, tile_h, C;
+};
+
+// 48-byte visible (view, surfel) record; layout documented in rogs.h.
+struct __align__(16) Record {
+    float mxi, myi, mxf, myf;
+    float ca, cb, cc, opacity;
+    float depth, key;
+    uint32_t surfel, view;
+};
+static_assert(sizeof(Record) == 48, "record layout");
+
+struct StateHeader {  // mirrors rogs_counts
+    unsigned long long n_records, n_pairs, need_records, need_pairs, composited;
+    unsigned int status, n_views;
+};
+static_assert(sizeof(StateHeader) == sizeof(rogs_counts), "header layout");
+
+enum : unsigned { kStatusRecordOverflow = 1u, kStatusPairOverflow = 2u };
+
+// ------------------------------------------------------------ double-float
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo);
+    return quick_two_sum(s.hi, lo);
+}
+
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    df s = two_sum(a.hi, b);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    df p = two_prod(a.hi, b);
+    return quick_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+
+// a / b for double-floats (one correction step, ~44 significant bits)
+__device__ __forceinline__ df df_div(df a, df b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    df qb = df_mul_f(b, q1);
+    df r = df_add(a, {-qb.hi, -qb.lo});
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    return quick_two_sum(q1, q2);
+}
+
+// --------------------------------------------------------------- binary32
+
+// ((r20 x + r21 y) + r22 z) + t2, rounded per operation; -0 -> +0.
+__device__ __forceinline__ float depth_key(const ViewParams& v, float x, float y, float z) {
+    float s = __fadd_rn(__fmul_rn(v.R[6], x), __fmul_rn(v.R[7], y));
+    s = __fadd_rn(s, __fmul_rn(v.R[8], z));
+    s = __fadd_rn(s, v.t[2]);
+    return __fadd_rn(s, 0.0f);
+}
+
+// Supplementary "Perspective Rendering Acceleration": keep surfels inside the
+// ground box +-box_half_x along the camera's ground-projected x axis and
+// [0, box_depth] along its ground-projected z axis, from the camera centre.
+__device__ __forceinline__ bool box_keep(const ViewParams& v, const Consts& k, float x, float y) {
+    if (!v.box || v.kind != ROGS_PERSP || !v.box_ok) return true;
+    float dx = __fsub_rn(x, v.ox);
+    float dy = __fsub_rn(y, v.oy);
+    float lat = __fadd_rn(__fmul_rn(dx, v.xh0), __fmul_rn(dy, v.xh1));
+    float fwd = __fadd_rn(__fmul_rn(dx, v.zh0), __fmul_rn(dy, v.zh1));
+    return (fabsf(lat) <= k.box_half_x) && (fwd >= 0.0f) && (fwd <= k.box_depth);
+}
+
+// Order-preserving map of a float to uint32 (ascending).
+__device__ __forceinline__ uint32_t float_sort_bits(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Offset of a pixel centre from a split mean: ((u + 0.5) - mean_int) - mean_frac.
+__device__ __forceinline__ float pix_offset(float pc, float mi, float mf) {
+    return __fsub_rn(__fsub_rn(pc, mi), mf);
+}
+
+// Per-pixel opacity a = min(alpha_max, alpha * exp(power)) with
+// power = -0.5 (A dx^2 + 2 B dx dy + C dy^2).  Written with explicit fused
+// operations so that the forward and the backward kernels evaluate it
+// bit-identically.  Returns a; g receives exp(power).
+__device__ __forceinline__ float surfel_alpha(float dx, float dy, float A, float B, float C, float alpha,
+                                              float alpha_max, float& g) {
+    float q = __fmaf_rn(__fmul_rn(A, dx), dx, __fmaf_rn(__fmul_rn(C, dy), dy, __fmul_rn(__fmul_rn(2.0f, B), __fmul_rn(dx, dy))));
+    g = __expf(__fmul_rn(-0.5f, q));
+    return fminf(alpha_max, __fmul_rn(alpha, g));
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Binary search of the view owning global tile t (tile_base ascending).
+__device__ __forceinline__ int view_of_tile(const ViewParams* views, int n_views, long long t) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (views[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace rogs

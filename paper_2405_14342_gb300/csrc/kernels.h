@@ -1,0 +1,82 @@
+// kernels.h -- host launchers of the librogs kernels (internal interface
+// between the C-ABI in api.cu and the kernel translation units).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace rogs {
+
+struct SurfelPtrs {
+    const float *xyz, *scale, *quat, *opacity, *rgb, *sem;
+    long long n;
+};
+
+struct GradPtrs {
+    float *xyz, *scale, *quat, *opacity, *rgb, *sem, *exposure;
+};
+
+// ---- sort.cu
+size_t radix_hist_words(unsigned long long cap);
+void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t* kalt,
+                      uint32_t* valt, const unsigned long long* n_ptr, unsigned long long cap, int key_bits,
+                      uint32_t* hist, cudaStream_t s);
+
+// ---- project.cu
+// Upload per-view parameters into device memory (by-value kernel argument).
+void upload_views(const ViewsArg& va, int n_views, ViewParams* dst, StateHeader* hdr, cudaStream_t s);
+// Cull + visibility bitmask: bits[v * n_words + w] bit l <=> surfel 32w+l visible in view v.
+void cull_views(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, uint32_t* bits, long long n_words,
+                cudaStream_t s);
+// Record positions: exclusive scan of popc(bits) (view-major) -> word_off; total -> hdr->need_records.
+void scan_visible(const uint32_t* bits, long long n_words_total, uint32_t* word_off, uint32_t* tile_sums,
+                  StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s);
+size_t scan_tile_sums_words(unsigned long long cap);
+// Write records, rects, depth sort keys and values.
+void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, const uint32_t* bits,
+                     const uint32_t* word_off, long long n_words, Record* recs, uint2* rects, uint32_t* keys,
+                     uint32_t* vals, unsigned long long rec_cap, cudaStream_t s);
+
+// ---- bin.cu
+// Pair offsets per depth-sorted record; total -> hdr->need_pairs, n_pairs clamped.
+void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeader* hdr_n_records,
+                unsigned long long rec_cap, unsigned long long* pair_off, unsigned long long* tile_sums,
+                StateHeader* hdr, unsigned long long pair_cap, cudaStream_t s);
+void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Record* recs, const uint2* rects,
+                const unsigned long long* pair_off, const StateHeader* hdr, unsigned long long rec_cap,
+                uint32_t* pair_keys, uint32_t* pair_vals, unsigned long long pair_cap, cudaStream_t s);
+void tile_ranges(const uint32_t* sorted_tile, const StateHeader* hdr, unsigned long long pair_cap, uint2* ranges,
+                 cudaStream_t s);
+void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s);
+
+// ---- composite.cu
+int padded_channels(int C);
+void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
+                   Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
+                   const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
+                   cudaStream_t s);
+
+// ---- backward.cu
+int grad_channels(int C);  // per-record gradient stride (32 or 64)
+void composite_bwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
+                   Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
+                   const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,
+                   float* rec_grad, float* d_exposure, cudaStream_t s);
+void project_bwd(const ViewParams* views, Consts k, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
+                 unsigned long long rec_cap, float* rec_grad, int C, GradPtrs g, cudaStream_t s);
+
+// ---- loss.cu
+void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, int C, const float* out,
+                  const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c, float lambda_s,
+                  float* loss, float* grad_out, unsigned long long* counter, float* partials, int n_blocks_cap,
+                  cudaStream_t s);
+int loss_blocks(long long total_pixels);
+
+// ---- init.cu
+void init_from_poses(const float* grid_xy, long long n, const float* poses_dev, long long n_poses, int exact_plane,
+                     float* out_z, float* out_quat, int32_t* out_nearest, cudaStream_t s);
+
+}  // namespace rogs

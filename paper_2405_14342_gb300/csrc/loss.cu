@@ -1,0 +1,139 @@
+// loss.cu -- masked L1 colour and masked cross-entropy semantic loss
+// (RoGs Sec. 3.3.2, Eqs. 8 and 9, weighted as in Eq. 12) and its gradient
+// with respect to the rendered planes.
+//
+//   mask_count_k : |M| = number of mask pixels over all views
+//   loss_k       : per pixel, L1 over the three colour channels and the
+//                  log-softmax cross entropy of the C logits; writes dL/dout
+//                  (one thread per pixel, coalesced plane reads/writes) and a
+//                  per-block partial sum
+//   loss_final_k : deterministic sum of the partials (fixed order), / |M|
+#include "kernels.h"
+
+namespace rogs {
+
+constexpr int kLossThreads = 256;
+
+int loss_blocks(long long total_pixels) { return (int)((total_pixels + kLossThreads - 1) / kLossThreads); }
+
+__device__ __forceinline__ int view_of_pixel(const ViewParams* views, int n_views, long long p) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (views[mid].pix_base <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kLossThreads) mask_count_k(const uint8_t* __restrict__ mask, long long n,
+                                                             unsigned long long* __restrict__ counter) {
+    __shared__ unsigned int sh[kLossThreads / 32];
+    unsigned int c = 0;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+        c += mask[p] ? 1u : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kLossThreads / 32; ++w) t += sh[w];
+        if (t) atomicAdd(counter, t);
+    }
+}
+
+__global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restrict__ views, int n_views,
+                                                       long long total_pixels, int C, const float* __restrict__ out,
+                                                       const float* __restrict__ tgt_rgb,
+                                                       const int32_t* __restrict__ label,
+                                                       const uint8_t* __restrict__ mask, float lambda_c,
+                                                       float lambda_s, const unsigned long long* __restrict__ counter,
+                                                       float* __restrict__ grad_out, float* __restrict__ partials) {
+    __shared__ float sh[kLossThreads / 32];
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (p < total_pixels) {
+        const int vi = view_of_pixel(views, n_views, p);
+        const ViewParams& v = views[vi];
+        const long long q = p - v.pix_base;
+        const long long plane = (long long)v.W * v.H;
+        const int nch = 3 + C + 1;
+        const float* o = out + (long long)nch * v.pix_base + q;
+        float* g = grad_out + (long long)nch * v.pix_base + q;
+        const unsigned long long nm = *counter;
+        const bool m = mask[p] != 0 && nm > 0;
+        if (!m) {
+            for (int ch = 0; ch < nch; ++ch) g[ch * plane] = 0.0f;
+        } else {
+            const float inv = 1.0f / (float)nm;
+            const float* t = tgt_rgb + 3ll * v.pix_base + q;
+            float l1 = 0.0f;
+            for (int ch = 0; ch < 3; ++ch) {
+                const float d = o[ch * plane] - t[ch * plane];
+                l1 += fabsf(d);
+                g[ch * plane] = lambda_c * inv * (d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f));
+            }
+            float ce = 0.0f;
+            const int lb = C > 0 ? label[p] : -1;
+            if (lb >= 0 && lb < C) {  // labels outside [0, C) carry no semantic term
+                float mx = o[3 * plane];
+                for (int ch = 1; ch < C; ++ch) mx = fmaxf(mx, o[(3 + ch) * plane]);
+                float se = 0.0f;
+                for (int ch = 0; ch < C; ++ch) se += expf(o[(3 + ch) * plane] - mx);
+                const float lse = mx + logf(se);
+                ce = lse - o[(3 + lb) * plane];
+                for (int ch = 0; ch < C; ++ch) {
+                    const float sm = expf(o[(3 + ch) * plane] - lse);
+                    g[(3 + ch) * plane] = lambda_s * inv * (sm - (ch == lb ? 1.0f : 0.0f));
+                }
+            } else {
+                for (int ch = 0; ch < C; ++ch) g[(3 + ch) * plane] = 0.0f;
+            }
+            g[(3 + C) * plane] = 0.0f;
+            l = lambda_c * l1 + lambda_s * ce;
+        }
+    }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) l += __shfl_xor_sync(kFull, l, o2);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < kLossThreads / 32; ++w) t += sh[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+__global__ void loss_final_k(const float* __restrict__ partials, int n, const unsigned long long* __restrict__ counter,
+                             float* __restrict__ loss) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)partials[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long nm = *counter;
+        loss[0] = nm ? (float)(sh[0] / (double)nm) : 0.0f;
+    }
+}
+
+void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, int C, const float* out,
+                  const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c, float lambda_s,
+                  float* loss, float* grad_out, unsigned long long* counter, float* partials, int n_blocks_cap,
+                  cudaStream_t s) {
+    const int nb = loss_blocks(total_pixels);
+    cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    int gc = nb < 152 * 8 ? nb : 152 * 8;
+    if (gc < 1) gc = 1;
+    mask_count_k<<<gc, kLossThreads, 0, s>>>(mask, total_pixels, counter);
+    loss_k<<<nb > 0 ? nb : 1, kLossThreads, 0, s>>>(views, n_views, total_pixels, C, out, tgt_rgb, label, mask,
+                                                    lambda_c, lambda_s, counter, grad_out, partials);
+    loss_final_k<<<1, 256, 0, s>>>(partials, nb, counter, loss);
+    (void)n_blocks_cap;
+}
+
+}  // namespace rogs

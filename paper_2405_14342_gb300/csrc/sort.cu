@@ -1,0 +1,204 @@
+// sort.cu -- hand-written stable LSD radix sort of (uint32 key, uint32 value)
+// pairs with a device-resident length (8-bit digits, 4096-key tiles).
+//
+// Per pass, three launches with fixed grids:
+//   rs_upsweep_k   per-tile digit histograms, digit-major [256][tiles]
+//   rs_rowscan_k   one block per digit: exclusive scan across tiles + digit total
+//   rs_downsweep_k stable scatter: the rank of a key inside its tile is built
+//                  warp by warp in key order (__match_any_sync groups equal
+//                  digits, lanes below a lane come first), then warps in
+//                  order, so equal keys keep their input order.
+// No block waits on another block.  Used for the depth sort of visible
+// records and the tile sort of (tile, record) pairs (RoGs Sec. 3.3.1: sort by
+// ascending original depth; ties by surfel index come from stability).
+#include "kernels.h"
+#include "scan.cuh"
+
+namespace rogs {
+
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsIpt = 16;
+constexpr int kRsWarpItems = 32 * kRsIpt;
+constexpr int kRsTile = kRsThreads * kRsIpt;  // 4096 keys
+
+__device__ __forceinline__ unsigned long long rs_len(const unsigned long long* n_ptr, unsigned long long cap) {
+    return scan_len(n_ptr, cap);
+}
+
+__global__ void __launch_bounds__(kRsThreads) rs_upsweep_k(const uint32_t* __restrict__ keys,
+                                                            const unsigned long long* n_ptr, unsigned long long cap,
+                                                            int shift, uint32_t mask, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t sh[kRsWarps][256];
+    const unsigned long long n = rs_len(n_ptr, cap);
+    const unsigned ntiles = (unsigned)((n + kRsTile - 1) / kRsTile);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+#pragma unroll
+        for (int w = 0; w < kRsWarps; ++w) sh[w][threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned long long base = (unsigned long long)tile * kRsTile + (unsigned long long)warp * kRsWarpItems;
+#pragma unroll 4
+        for (int k = 0; k < kRsIpt; ++k) {
+            unsigned long long i = base + k * 32 + lane;
+            if (i < n) atomicAdd(&sh[warp][(keys[i] >> shift) & mask], 1u);
+        }
+        __syncthreads();
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kRsWarps; ++w) s += sh[w][threadIdx.x];
+        hist[(unsigned long long)threadIdx.x * ntiles + tile] = s;
+        __syncthreads();
+    }
+}
+
+// One block per digit: exclusive scan of hist[d][0..ntiles) in place.
+__global__ void __launch_bounds__(kScanThreads) rs_rowscan_k(uint32_t* __restrict__ hist,
+                                                              const unsigned long long* n_ptr, unsigned long long cap,
+                                                              uint32_t* __restrict__ row_total) {
+    __shared__ uint32_t sh[33];
+    const unsigned long long n = rs_len(n_ptr, cap);
+    const unsigned ntiles = (unsigned)((n + kRsTile - 1) / kRsTile);
+    uint32_t* row = hist + (unsigned long long)blockIdx.x * ntiles;
+    uint32_t carry = 0;
+    for (unsigned base = 0; base < ntiles; base += kScanThreads) {
+        unsigned i = base + threadIdx.x;
+        uint32_t v = i < ntiles ? row[i] : 0u;
+        uint32_t tot;
+        uint32_t ex = block_excl_scan<uint32_t>(v, sh, tot);
+        if (i < ntiles) row[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) row_total[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __restrict__ kin,
+                                                              const uint32_t* __restrict__ vin,
+                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                              const unsigned long long* n_ptr, unsigned long long cap,
+                                                              int shift, uint32_t mask, const uint32_t* __restrict__ hist,
+                                                              const uint32_t* __restrict__ row_total) {
+    __shared__ uint32_t digit_base[256];
+    __shared__ uint32_t wh[kRsWarps][256];
+    __shared__ uint32_t scan_w[kRsWarps + 1];
+    const unsigned long long n = rs_len(n_ptr, cap);
+    const unsigned ntiles = (unsigned)((n + kRsTile - 1) / kRsTile);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+
+    // exclusive scan of the 256 digit totals
+    {
+        uint32_t v = row_total[threadIdx.x];
+        uint32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) scan_w[warp] = inc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t c = 0;
+            for (int w = 0; w < kRsWarps; ++w) { uint32_t t = scan_w[w]; scan_w[w] = c; c += t; }
+        }
+        __syncthreads();
+        digit_base[threadIdx.x] = scan_w[warp] + inc - v;
+        __syncthreads();
+    }
+
+    for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+#pragma unroll
+        for (int w = 0; w < kRsWarps; ++w) wh[w][threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned long long base = (unsigned long long)tile * kRsTile + (unsigned long long)warp * kRsWarpItems;
+        uint32_t key[kRsIpt], val[kRsIpt], rank[kRsIpt];
+#pragma unroll
+        for (int k = 0; k < kRsIpt; ++k) {
+            unsigned long long i = base + k * 32 + lane;
+            bool valid = i < n;
+            key[k] = valid ? kin[i] : 0u;
+            val[k] = valid ? vin[i] : 0u;
+            unsigned vm = __ballot_sync(kFull, valid);
+            uint32_t d = (key[k] >> shift) & mask;
+            unsigned peers = 0;
+            rank[k] = 0;
+            if (valid) {
+                peers = __match_any_sync(vm, d);
+                rank[k] = wh[warp][d] + __popc(peers & lt);
+            }
+            __syncwarp();
+            if (valid && (peers & lt) == 0) wh[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            const int d = threadIdx.x;
+            uint32_t run = digit_base[d] + hist[(unsigned long long)d * ntiles + tile];
+#pragma unroll
+            for (int w = 0; w < kRsWarps; ++w) {
+                uint32_t c = wh[w][d];
+                wh[w][d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kRsIpt; ++k) {
+            unsigned long long i = base + k * 32 + lane;
+            if (i < n) {
+                uint32_t d = (key[k] >> shift) & mask;
+                uint32_t pos = wh[warp][d] + rank[k];
+                kout[pos] = key[k];
+                vout[pos] = val[k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void copy_pairs_k(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
+                             const unsigned long long* n_ptr, unsigned long long cap) {
+    const unsigned long long n = rs_len(n_ptr, cap);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        kout[i] = kin[i];
+        vout[i] = vin[i];
+    }
+}
+
+size_t radix_hist_words(unsigned long long cap) {
+    unsigned long long t = (cap + kRsTile - 1) / kRsTile;
+    if (t == 0) t = 1;
+    return (size_t)(256 * t + 256);
+}
+
+void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t* kalt,
+                      uint32_t* valt, const unsigned long long* n_ptr, unsigned long long cap, int key_bits,
+                      uint32_t* hist, cudaStream_t s) {
+    uint32_t* row_total = hist + (radix_hist_words(cap) - 256);
+    int passes = (key_bits + 7) / 8;
+    unsigned long long tiles = (cap + kRsTile - 1) / kRsTile;
+    int grid = (int)(tiles < 1 ? 1 : (tiles > 2048 ? 2048 : tiles));
+    if (passes == 0) {
+        copy_pairs_k<<<grid, 256, 0, s>>>(kin, vin, kout, vout, n_ptr, cap);
+        return;
+    }
+    const uint32_t* sk = kin;
+    const uint32_t* sv = vin;
+    for (int p = 0; p < passes; ++p) {
+        // the last pass must land in (kout, vout)
+        bool to_out = ((passes - 1 - p) % 2) == 0;
+        uint32_t* dk = to_out ? kout : kalt;
+        uint32_t* dv = to_out ? vout : valt;
+        int shift = 8 * p;
+        int bits = key_bits - shift < 8 ? key_bits - shift : 8;
+        uint32_t mask = (bits >= 32) ? 0xffffffffu : ((1u << bits) - 1u);
+        rs_upsweep_k<<<grid, kRsThreads, 0, s>>>(sk, n_ptr, cap, shift, mask, hist);
+        rs_rowscan_k<<<256, kScanThreads, 0, s>>>(hist, n_ptr, cap, row_total);
+        rs_downsweep_k<<<grid, kRsThreads, 0, s>>>(sk, sv, dk, dv, n_ptr, cap, shift, mask, hist, row_total);
+        sk = dk;
+        sv = dv;
+    }
+}
+
+}  // namespace rogs

@@ -1,0 +1,197 @@
+"""PyTorch front end of librogs: device memory, streams and autograd only.
+
+Every step of the method (projection, binning and sorting, compositing,
+loss, backward, initialisation) runs in librogs' CUDA kernels through the
+C-ABI binding in ``rogs``; this module allocates tensors, passes pointers and
+wraps the forward/backward pair in a ``torch.autograd.Function``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import rogs as R
+
+
+@dataclasses.dataclass
+class SurfelTensors:
+    """Device copy of a surfel map (Sec. 3.1, Eq. 3): xyz [N,3], scale [N,2],
+    quat [N,4], opacity [N], rgb [N,3], sem [N,C] (FP32, contiguous)."""
+    xyz: torch.Tensor
+    scale: torch.Tensor
+    quat: torch.Tensor
+    opacity: torch.Tensor
+    rgb: torch.Tensor
+    sem: torch.Tensor
+
+    @staticmethod
+    def from_map(m, device="cuda") -> "SurfelTensors":
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=device).contiguous()
+        return SurfelTensors(f(m.xyz), f(m.scale), f(m.quat), f(m.opacity), f(m.rgb), f(m.sem))
+
+    @property
+    def n(self) -> int:
+        return int(self.xyz.shape[0])
+
+    def tensors(self):
+        return (self.xyz, self.scale, self.quat, self.opacity, self.rgb, self.sem)
+
+    def c_struct(self) -> R.rogs_surfels:
+        return R.surfels(self.xyz, self.scale, self.quat, self.opacity, self.rgb, self.sem)
+
+
+@dataclasses.dataclass
+class Frame:
+    """Output and state of one forward call over a fixed set of cameras."""
+    cams: list
+    cam_arr: object
+    layout: R.rogs_state_layout
+    out: torch.Tensor       # float[(3+C+1) * total_pixels]
+    state: torch.Tensor     # uint8[layout.total_bytes]
+    pix_base: List[int]
+
+    def view(self, v: int, C: int) -> torch.Tensor:
+        """Planes [3+C+1, H, W] of view v."""
+        c = self.cams[v]
+        nch = 3 + C + 1
+        b = nch * self.pix_base[v]
+        return self.out[b: b + nch * c.width * c.height].view(nch, c.height, c.width)
+
+    def state_section(self, name: str, dtype, count: int) -> torch.Tensor:
+        off = getattr(self.layout, name)
+        itemsize = torch.empty(0, dtype=dtype).element_size()
+        return self.state[off: off + count * itemsize].view(dtype)
+
+
+def _aligned_bytes(nbytes: int, device) -> torch.Tensor:
+    t = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-t.data_ptr()) % 256
+    return t[off: off + nbytes]
+
+
+class Renderer:
+    """Owns one librogs context (scratch, capacities, constants)."""
+
+    def __init__(self, num_classes: int, record_capacity: int = 1 << 20, pair_capacity: int = 1 << 22,
+                 tile=(16, 16), device="cuda", **consts):
+        self.C = int(num_classes)
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.cfg = R.rogs_default_config(self.C, int(record_capacity), int(pair_capacity),
+                                             tile_w=int(tile[0]), tile_h=int(tile[1]), **consts)
+            self.ctx = R.rogs_create(self.cfg)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            R.rogs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nch(self) -> int:
+        return 3 + self.C + 1
+
+    def reserve(self, n_surfels: int, n_views: int):
+        R.rogs_reserve(self.ctx, n_surfels, n_views)
+
+    def frame(self, cams: Sequence) -> Frame:
+        arr = R.cameras(cams)
+        L, elems = R.rogs_state_layout_of(self.ctx, arr, len(cams))
+        out = torch.empty(elems, dtype=torch.float32, device=self.device)
+        state = _aligned_bytes(int(L.total_bytes), self.device)
+        pix, acc = [], 0
+        for c in cams:
+            pix.append(acc)
+            acc += c.width * c.height
+        return Frame(list(cams), arr, L, out, state, pix)
+
+    # -- the C-ABI calls --------------------------------------------------
+
+    def forward(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, stream=None) -> Frame:
+        R.rogs_render_fwd(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
+                          frame.state, stream)
+        return frame
+
+    def counts(self, frame: Frame, stream=None, check=True) -> R.rogs_counts:
+        return R.rogs_state_counts(self.ctx, frame.state, stream, check=check)
+
+    def loss(self, frame: Frame, tgt_rgb, label, mask, lambda_c=1.0, lambda_s=0.06, loss=None, grad_out=None,
+             stream=None):
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        if grad_out is None:
+            grad_out = torch.empty_like(frame.out)
+        R.rogs_loss(self.ctx, frame.cam_arr, len(frame.cams), frame.out, tgt_rgb, label, mask, lambda_c, lambda_s,
+                    loss, grad_out, stream)
+        return loss, grad_out
+
+    def backward(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, grad_out: torch.Tensor,
+                 grads: Optional[dict] = None, stream=None) -> dict:
+        if grads is None:
+            grads = zero_grads(m, exposure)
+        g = R.rogs_grads()
+        for k in ("xyz", "scale", "quat", "opacity", "rgb", "sem", "exposure"):
+            t = grads.get(k)
+            setattr(g, k, t.data_ptr() if t is not None and t.numel() else None)
+        R.rogs_render_bwd(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.state,
+                          grad_out.contiguous(), g, stream)
+        return grads
+
+    def init_from_poses(self, grid_xy: torch.Tensor, poses: np.ndarray, exact_plane=True, stream=None):
+        n = grid_xy.shape[0]
+        z = torch.empty(n, dtype=torch.float32, device=self.device)
+        q = torch.empty(n, 4, dtype=torch.float32, device=self.device)
+        near = torch.empty(n, dtype=torch.int32, device=self.device)
+        R.rogs_init_from_poses(self.ctx, grid_xy.contiguous(), poses, exact_plane, z, q, near, stream)
+        return z, q, near
+
+    def sort_pairs(self, keys: torch.Tensor, vals: torch.Tensor, key_bits: int = 32, stream=None):
+        ko = torch.empty_like(keys)
+        vo = torch.empty_like(vals)
+        R.rogs_sort_pairs(self.ctx, keys, vals, key_bits, ko, vo, stream)
+        return ko, vo
+
+
+def zero_grads(m: SurfelTensors, exposure: torch.Tensor) -> dict:
+    return dict(xyz=torch.zeros_like(m.xyz), scale=torch.zeros_like(m.scale), quat=torch.zeros_like(m.quat),
+                opacity=torch.zeros_like(m.opacity), rgb=torch.zeros_like(m.rgb), sem=torch.zeros_like(m.sem),
+                exposure=torch.zeros_like(exposure))
+
+
+def targets_to_device(targets, device="cuda"):
+    """Per-view planar targets -> flat device tensors in the output pixel order."""
+    # planar per view: [3][pixels of view] blocks, view after view
+    rgb = torch.cat([torch.as_tensor(np.ascontiguousarray(t, np.float32)).reshape(-1) for t in targets.rgb]).to(device)
+    label = torch.cat([torch.as_tensor(np.ascontiguousarray(l, np.int32)).reshape(-1) for l in targets.label]).to(device)
+    mask = torch.cat([torch.as_tensor(np.ascontiguousarray(k, np.uint8)).reshape(-1) for k in targets.mask]).to(device)
+    return rgb.contiguous(), label.contiguous(), mask.contiguous()
+
+
+class RenderFunction(torch.autograd.Function):
+    """out = render(surfels, exposure); backward via rogs_render_bwd."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, frame: Frame, xyz, scale, quat, opacity, rgb, sem, exposure):
+        m = SurfelTensors(xyz.detach(), scale.detach(), quat.detach(), opacity.detach(), rgb.detach(), sem.detach())
+        renderer.forward(m, frame, exposure.detach())
+        ctx.renderer, ctx.frame, ctx.m, ctx.exposure = renderer, frame, m, exposure.detach()
+        return frame.out.clone()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = ctx.renderer.backward(ctx.m, ctx.frame, ctx.exposure, grad_out.contiguous())
+        return (None, None, g["xyz"], g["scale"], g["quat"], g["opacity"], g["rgb"], g["sem"], g["exposure"])
+
+
+def render(renderer: Renderer, cams, xyz, scale, quat, opacity, rgb, sem, exposure, frame: Frame = None):
+    """Differentiable render of `cams`; returns the flat output planes."""
+    frame = renderer.frame(cams) if frame is None else frame
+    return RenderFunction.apply(renderer, frame, xyz, scale, quat, opacity, rgb, sem, exposure), frame

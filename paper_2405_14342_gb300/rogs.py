@@ -1,0 +1,222 @@
+"""ctypes binding of librogs (include/rogs.h), same names as the C-ABI.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of librogs.so.  Importing this module loads the in-tree library and
+raises if it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librogs.so")
+
+ROGS_OK, ROGS_ERR_INVALID, ROGS_ERR_CAPACITY, ROGS_ERR_OOM = 0, 1, 2, 3
+ROGS_ERR_CUDA, ROGS_ERR_TIMEOUT, ROGS_ERR_BUSY, ROGS_ERR_NOT_READY = 4, 5, 6, 7
+ROGS_PERSP, ROGS_ORTHO = 0, 1
+ROGS_MAX_VIEWS = 128
+ROGS_MAX_CLASSES = 54
+
+STATUS_NAMES = {0: "ROGS_OK", 1: "ROGS_ERR_INVALID", 2: "ROGS_ERR_CAPACITY", 3: "ROGS_ERR_OOM",
+                4: "ROGS_ERR_CUDA", 5: "ROGS_ERR_TIMEOUT", 6: "ROGS_ERR_BUSY", 7: "ROGS_ERR_NOT_READY"}
+
+
+class RogsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rogs_config(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("num_classes", C.c_int32),
+                ("t_min", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
+                ("eps_dilate", C.c_float), ("near_plane", C.c_float), ("box_half_x", C.c_float),
+                ("box_depth", C.c_float), ("jac_clamp", C.c_float),
+                ("record_capacity", C.c_int64), ("pair_capacity", C.c_int64)]
+
+
+class rogs_camera(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("exposure_idx", C.c_int32),
+                ("use_box_cull", C.c_int32), ("reserved", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("R_wc", C.c_float * 9), ("t_wc", C.c_float * 3)]
+
+
+class rogs_surfels(C.Structure):
+    _fields_ = [("xyz", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("opacity", C.c_void_p),
+                ("rgb", C.c_void_p), ("sem", C.c_void_p), ("n", C.c_int64)]
+
+
+class rogs_grads(C.Structure):
+    _fields_ = [("xyz", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("opacity", C.c_void_p),
+                ("rgb", C.c_void_p), ("sem", C.c_void_p), ("exposure", C.c_void_p)]
+
+
+class rogs_counts(C.Structure):
+    _fields_ = [("n_records", C.c_uint64), ("n_pairs", C.c_uint64), ("need_records", C.c_uint64),
+                ("need_pairs", C.c_uint64), ("composited", C.c_uint64), ("status", C.c_uint32),
+                ("n_views", C.c_uint32)]
+
+
+class rogs_state_layout(C.Structure):
+    _fields_ = [("header", C.c_uint64), ("records", C.c_uint64), ("rects", C.c_uint64), ("pair_rec", C.c_uint64),
+                ("tile_range", C.c_uint64), ("pix_T", C.c_uint64), ("pix_last", C.c_uint64),
+                ("views", C.c_uint64), ("total_bytes", C.c_uint64), ("total_tiles", C.c_int64),
+                ("total_pixels", C.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded librogs (raises if the extension was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"librogs.so not built at {LIB_PATH}; run __graft_entry__.build() "
+                               "(python -m paper_2405_14342_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        P, S = C.c_void_p, C.c_int
+        L.rogs_default_config.argtypes = [C.c_int32, C.c_int64, C.c_int64, C.POINTER(rogs_config)]
+        L.rogs_create.argtypes = [C.POINTER(rogs_config), C.POINTER(P)]
+        L.rogs_destroy.argtypes = [P]
+        L.rogs_destroy.restype = None
+        L.rogs_last_error.argtypes = [P]
+        L.rogs_last_error.restype = C.c_char_p
+        L.rogs_reserve.argtypes = [P, C.c_int64, C.c_int32]
+        L.rogs_state_layout_of.argtypes = [P, C.POINTER(rogs_camera), C.c_int32, C.POINTER(rogs_state_layout),
+                                           C.POINTER(C.c_uint64)]
+        L.rogs_state_counts.argtypes = [P, P, C.POINTER(rogs_counts), P]
+        L.rogs_init_from_poses.argtypes = [P, P, C.c_int64, P, C.c_int64, C.c_int32, P, P, P, P]
+        L.rogs_render_fwd.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
+                                      P, P, P]
+        L.rogs_loss.argtypes = [P, C.POINTER(rogs_camera), C.c_int32, P, P, P, P, C.c_float, C.c_float, P, P, P]
+        L.rogs_render_bwd.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
+                                      P, P, C.POINTER(rogs_grads), P]
+        L.rogs_sort_pairs.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P, P]
+        for name in ("rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
+                     "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
+                     "rogs_render_bwd", "rogs_sort_pairs"):
+            getattr(L, name).restype = S
+        _lib = L
+    return _lib
+
+
+def _check(ctx, st):
+    if st != ROGS_OK:
+        msg = lib().rogs_last_error(ctx).decode() if ctx else ""
+        raise RogsError(st, msg)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def cameras(cams) -> "C.Array":
+    """Build a rogs_camera array from objects with kind/width/height/fx/fy/cx/cy/R/t/
+    exposure_idx/use_box_cull attributes (e.g. scenes.Camera)."""
+    arr = (rogs_camera * len(cams))()
+    for i, c in enumerate(cams):
+        a = arr[i]
+        a.kind, a.width, a.height = int(c.kind), int(c.width), int(c.height)
+        a.exposure_idx, a.use_box_cull, a.reserved = int(c.exposure_idx), int(c.use_box_cull), 0
+        a.fx, a.fy, a.cx, a.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        R = np.asarray(c.R, dtype=np.float32).ravel()
+        t = np.asarray(c.t, dtype=np.float32).ravel()
+        for k in range(9):
+            a.R_wc[k] = float(R[k])
+        for k in range(3):
+            a.t_wc[k] = float(t[k])
+    return arr
+
+
+def surfels(xyz, scale, quat, opacity, rgb, sem) -> rogs_surfels:
+    s = rogs_surfels()
+    s.xyz, s.scale, s.quat, s.opacity = xyz.data_ptr(), scale.data_ptr(), quat.data_ptr(), opacity.data_ptr()
+    s.rgb, s.sem = rgb.data_ptr(), (sem.data_ptr() if sem is not None and sem.numel() else None)
+    s.n = int(xyz.shape[0])
+    return s
+
+
+# ----------------------------------------------------------------- calls
+
+def rogs_default_config(num_classes, record_capacity, pair_capacity, **over) -> rogs_config:
+    cfg = rogs_config()
+    _check(None, lib().rogs_default_config(num_classes, record_capacity, pair_capacity, C.byref(cfg)))
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def rogs_create(cfg: rogs_config):
+    h = C.c_void_p()
+    st = lib().rogs_create(C.byref(cfg), C.byref(h))
+    if st != ROGS_OK:
+        raise RogsError(st, "rogs_create failed")
+    return h
+
+
+def rogs_destroy(ctx):
+    lib().rogs_destroy(ctx)
+
+
+def rogs_last_error(ctx) -> str:
+    return lib().rogs_last_error(ctx).decode()
+
+
+def rogs_reserve(ctx, n_surfels, n_views):
+    _check(ctx, lib().rogs_reserve(ctx, int(n_surfels), int(n_views)))
+
+
+def rogs_state_layout_of(ctx, cam_arr, n_views):
+    L = rogs_state_layout()
+    elems = C.c_uint64()
+    _check(ctx, lib().rogs_state_layout_of(ctx, cam_arr, n_views, C.byref(L), C.byref(elems)))
+    return L, int(elems.value)
+
+
+def rogs_state_counts(ctx, state, stream=None, check=True) -> rogs_counts:
+    c = rogs_counts()
+    st = lib().rogs_state_counts(ctx, _ptr(state), C.byref(c), _stream(stream))
+    if check:
+        _check(ctx, st)
+    return c
+
+
+def rogs_init_from_poses(ctx, grid_xy, poses_host: np.ndarray, exact_plane, out_z, out_quat, out_nearest=None,
+                         stream=None):
+    poses_host = np.ascontiguousarray(poses_host, dtype=np.float32).reshape(-1, 12)
+    _check(ctx, lib().rogs_init_from_poses(ctx, _ptr(grid_xy), int(grid_xy.shape[0]),
+                                           poses_host.ctypes.data_as(C.c_void_p), int(poses_host.shape[0]),
+                                           int(bool(exact_plane)), _ptr(out_z), _ptr(out_quat), _ptr(out_nearest),
+                                           _stream(stream)))
+
+
+def rogs_render_fwd(ctx, surf: rogs_surfels, cam_arr, n_views, exposure_ab, out, state, stream=None):
+    _check(ctx, lib().rogs_render_fwd(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
+                                      int(exposure_ab.shape[0]), _ptr(out), _ptr(state), _stream(stream)))
+
+
+def rogs_loss(ctx, cam_arr, n_views, out, tgt_rgb, label, mask, lambda_c, lambda_s, loss, grad_out, stream=None):
+    _check(ctx, lib().rogs_loss(ctx, cam_arr, n_views, _ptr(out), _ptr(tgt_rgb), _ptr(label), _ptr(mask),
+                                float(lambda_c), float(lambda_s), _ptr(loss), _ptr(grad_out), _stream(stream)))
+
+
+def rogs_render_bwd(ctx, surf: rogs_surfels, cam_arr, n_views, exposure_ab, state, grad_out, grads: rogs_grads,
+                    stream=None):
+    _check(ctx, lib().rogs_render_bwd(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
+                                      int(exposure_ab.shape[0]), _ptr(state), _ptr(grad_out), C.byref(grads),
+                                      _stream(stream)))
+
+
+def rogs_sort_pairs(ctx, keys_in, vals_in, key_bits, keys_out, vals_out, stream=None):
+    _check(ctx, lib().rogs_sort_pairs(ctx, _ptr(keys_in), _ptr(vals_in), int(keys_in.numel()), int(key_bits),
+                                      _ptr(keys_out), _ptr(vals_out), _stream(stream)))

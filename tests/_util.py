@@ -1,0 +1,76 @@
+"""Shared test helpers: layout conversions between the CUDA path's planar
+outputs / state buffer and the oracle's pixel lists.  Nothing here computes
+any part of the method."""
+import numpy as np
+
+RECORD_DTYPE = np.dtype([("mxi", "<f4"), ("myi", "<f4"), ("mxf", "<f4"), ("myf", "<f4"),
+                         ("ca", "<f4"), ("cb", "<f4"), ("cc", "<f4"), ("opacity", "<f4"),
+                         ("depth", "<f4"), ("key", "<f4"), ("surfel", "<u4"), ("view", "<u4")])
+
+
+def gpu_pixels(frame, C, pix):
+    """GPU output planes gathered at an oracle pixel list (v,u,y) -> (n, 3+C+1) float64."""
+    outs = [frame.view(v, C).cpu().numpy() for v in range(len(frame.cams))]
+    res = np.zeros((pix.shape[0], 3 + C + 1))
+    for v in np.unique(pix[:, 0]):
+        s = pix[:, 0] == v
+        res[s] = outs[v][:, pix[s, 2], pix[s, 1]].T
+    return res
+
+
+def pixel_index(frame, pix):
+    """Global pixel index of an oracle pixel list."""
+    base = np.array(frame.pix_base)
+    W = np.array([c.width for c in frame.cams])
+    return base[pix[:, 0]] + pix[:, 2] * W[pix[:, 0]] + pix[:, 1]
+
+
+def gpu_state_T(frame):
+    import torch
+    return frame.state_section("pix_T", torch.float32, frame.layout.total_pixels).cpu().numpy()
+
+
+def gpu_records(frame, counts):
+    import torch
+    n = int(counts.n_records)
+    raw = frame.state_section("records", torch.uint8, 48 * n).cpu().numpy()
+    return np.frombuffer(raw.tobytes(), dtype=RECORD_DTYPE).copy()
+
+
+def gpu_rects(frame, counts):
+    import torch
+    n = int(counts.n_records)
+    r = frame.state_section("rects", torch.int32, 2 * n).cpu().numpy().view(np.uint32).reshape(n, 2)
+    x0, y0 = r[:, 0] & 0xFFFF, r[:, 0] >> 16
+    x1, y1 = r[:, 1] & 0xFFFF, r[:, 1] >> 16
+    return np.stack([x0, y0, x1, y1], -1).astype(np.int32)
+
+
+def gpu_tile_lists(frame, counts):
+    import torch
+    K = int(counts.n_pairs)
+    T = int(frame.layout.total_tiles)
+    pr = frame.state_section("pair_rec", torch.int32, K).cpu().numpy().view(np.uint32).astype(np.int64)
+    rg = frame.state_section("tile_range", torch.int32, 2 * T).cpu().numpy().view(np.uint32).reshape(T, 2)
+    return pr, rg.astype(np.int64)
+
+
+def planar_grad_from_pixels(frame, C, pix, g):
+    """Scatter a per-pixel (n, 3+C+1) gradient into the planar output layout."""
+    out = np.zeros(int(frame.out.numel()), np.float32)
+    nch = 3 + C + 1
+    for v in np.unique(pix[:, 0]):
+        c = frame.cams[v]
+        s = pix[:, 0] == v
+        blk = out[nch * frame.pix_base[v]: nch * (frame.pix_base[v] + c.width * c.height)].reshape(nch, c.height, c.width)
+        blk[:, pix[s, 2], pix[s, 1]] = g[s].T
+    return out
+
+
+def normwise(a, b):
+    """max|a-b| / max|b| (0 if both vanish)."""
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    m = np.abs(b).max() if b.size else 0.0
+    if m == 0.0:
+        return float(np.abs(a).max()) if a.size else 0.0
+    return float(np.abs(a - b).max() / m)
