@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark: fwd+bwd Mpix/s of meshgrid-surfel splatting at 1.6M surfels.
+
+Workload (default, "scene"): a 400 m x 40 m road strip at 0.1 m spacing
+(1.6M surfels, 19 semantic classes) on a smooth random height field; six
+960x540 surround pinhole cameras on a straight trajectory at 1.5 m height.
+One step = forward render of one timestep's six views (projection + cull,
+depth sort, tile binning and sort, compositing), the masked L1 + CE loss and
+the backward (reverse compositing + projection backward), all through the
+C-ABI of librogs.  Steps cycle over timesteps t = 8..39; the map and every
+timestep's targets are resident in HBM before timing (inputs larger than L2).
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded pixel sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s at 1.6M surfels; serve p50/p99 ms vs per-view plain path"
+T_FIRST, T_COUNT = 8, 32          # timesteps 8..39
+SM_COUNT, FP32_LANES = 152, 128   # GB300: 152 SMs x 128 FP32 lanes
+
+# Measured DRAM traffic (bytes per launch) of the dominant kernel from one ncu
+# capture, keyed by the sha256 of the source file it was taken from; a
+# different source hash means the kernel changed since and traffic is null.
+NCU_TRAFFIC = {}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d["hbm_gbs"], d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def file_sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.path = None
+        self.idx = device_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workload
+
+def build_workload(rank: int, C: int, world: int):
+    from paper_2405_14342_gb300 import scenes
+    m, field = scenes.strip_map(C=C, seed=0)
+    t0 = T_FIRST + 40 * rank          # each rank takes its own stretch of road (weak scaling)
+    rigs = [scenes.surround_rig(field, t0 + k) for k in range(T_COUNT)]
+    return m, field, rigs
+
+
+def make_targets(R, renderer, m_pert, rigs, exposure):
+    """Supervision rendered from the seed-perturbed map by the CUDA path:
+    rgb planes, label = argmax of the rendered semantics, mask = 1 - T >= 0.5."""
+    import torch
+    st = R.SurfelTensors.from_map(m_pert)
+    out = []
+    for cams in rigs:
+        fr = renderer.frame(cams)
+        renderer.forward(st, fr, exposure)
+        torch.cuda.synchronize()
+        renderer.counts(fr)
+        T = fr.state_section("pix_T", torch.float32, fr.layout.total_pixels)
+        rgbs, labels = [], []
+        for v, c in enumerate(cams):
+            pl = fr.view(v, renderer.C)
+            rgbs.append(pl[:3].reshape(-1))
+            labels.append(pl[3:3 + renderer.C].argmax(0).to(torch.int32).reshape(-1))
+        out.append((torch.cat(rgbs).contiguous(), torch.cat(labels).contiguous(),
+                    (T <= 0.5).to(torch.uint8).contiguous()))
+        del fr
+    del st
+    return out
+
+
+# --------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2405_14342_gb300 import render as R, rogs, scenes
+
+    C = 19
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    m, field, rigs = build_workload(rank, C, world)
+    exposure = torch.as_tensor(scenes.exposure_params(6), device="cuda")
+    rr = R.Renderer(C, record_capacity=args.record_capacity, pair_capacity=args.pair_capacity, tile=tile)
+    rr.reserve(m.n, 6)
+    targets = make_targets(R, rr, scenes.perturb(m, seed=1), rigs, exposure)
+    st = R.SurfelTensors.from_map(m)
+    del m
+    frames = [rr.frame(c) for c in rigs]
+    grads = R.zero_grads(st, exposure)
+    P = frames[0].layout.total_pixels
+    loss = torch.empty(1, device="cuda")
+    gout = torch.empty_like(frames[0].out)
+
+    def step(k):
+        fr = frames[k % T_COUNT]
+        trgb, lab, msk = targets[k % T_COUNT]
+        rr.forward(st, fr, exposure)
+        rr.loss(fr, trgb, lab, msk, 1.0, 0.06, loss=loss, grad_out=gout)
+        rr.backward(st, fr, exposure, gout, grads=grads)
+
+    # set-up: every timestep's forward must fit the capacities (raises otherwise)
+    for k in range(T_COUNT):
+        rr.forward(st, frames[k], exposure)
+    torch.cuda.synchronize()
+    for fr in frames:
+        rr.counts(fr)
+    # warm-up
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    sampler = ClockSampler(vis.split(",")[local] if vis else local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    rogs.rogs_profile_enable(rr.ctx, True)
+    launches0 = rogs.rogs_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = rogs.rogs_launch_count() - launches0
+    prof = rogs.rogs_profile_read(rr.ctx)
+    rogs.rogs_profile_enable(rr.ctx, False)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+
+    # per-step counts of the timed steps (deterministic per timestep)
+    comp, nrec, npair = 0, 0, 0
+    for k in range(args.steps):
+        c = rr.counts(frames[(args.warmup + k) % T_COUNT])
+        comp += c.composited
+        nrec += c.n_records
+        npair += c.n_pairs
+
+    # ---- end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = []
+        for k in range(min(8, T_COUNT)):
+            a, b, c = targets[k]
+            pinned.append((a.cpu().pin_memory(), b.cpu().pin_memory(), c.cpu().pin_memory()))
+        dev = [torch.empty_like(x) for x in targets[0]]
+        host_loss = torch.empty(1, pin_memory=True)
+        h2d = sum(int(x.numel() * x.element_size()) for x in pinned[0])
+
+        def step_host(k):
+            fr = frames[k % len(pinned)]
+            for d, h in zip(dev, pinned[k % len(pinned)]):
+                d.copy_(h, non_blocking=True)
+            rr.forward(st, fr, exposure)
+            rr.loss(fr, dev[0], dev[1], dev[2], 1.0, 0.06, loss=loss, grad_out=gout)
+            rr.backward(st, fr, exposure, gout, grads=grads)
+            host_loss.copy_(loss, non_blocking=True)
+
+        for k in range(max(args.warmup, 1)):
+            step_host(k)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for k in range(args.steps):
+            step_host(k)
+        a1.record()
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": round(world * args.steps * P / (ems * 1e-3) / 1e6, 3), "unit": "Mpix/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    value = world * args.steps * P / (ms * 1e-3) / 1e6
+    hbm, smmax, peak_kind = peaks()
+    nch = 3 + C + 1
+    E = comp / args.steps
+    nr = nrec / args.steps
+    K = npair / args.steps
+    # algorithmic work per launch of each stage
+    feat = 4 * (3 + C)
+    stage_work = {
+        "composite_fwd": (P * (4 * nch + 8) + 4 * K + nr * (48 + feat), E * (2 * nch + 18)),
+        "composite_bwd": (P * (4 * nch + 8) + 4 * K + nr * (48 + feat + 4 * (6 + nch)), E * (8 * nch + 33)),
+        "loss": (P * (4 * (3 + C) + 17 + 4 * nch), P * (8 * C + 12)),
+        "project_bwd": (nr * (4 * (6 + nch) + 48 + 40 + 4 * (10 + 3 + C)), nr * 200),
+        "cull_project": (st.n * 12 + st.n * 40 + nr * (48 + 8 + 8), st.n * 6 * 12 + nr * 300),
+        "depth_sort": (4 * nr * 24, 0.0),
+        "pair_emit": (nr * 24 + K * 8, 0.0),
+        "tile_sort": (2 * K * 24 + 8 * K, 0.0),
+    }
+    stage_ms = {k: (v[0] / max(v[1], 1)) for k, v in prof.items()}   # average per launch
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    alu_peak = SM_COUNT * FP32_LANES * 2 * smmax * 1e6 / 1e12      # TFLOP/s
+    b, f = stage_work[dom]
+    t = stage_ms[dom] * 1e-3
+    if f / (alu_peak * 1e12) > b / (hbm * 1e9):
+        roof = {"bound": "alu", "achieved": round(f / t / 1e12, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(b / t / 1e9, 1), "peak": hbm, "unit": "GB/s"}
+    roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
+    roof["kernel"] = dom
+    roof["peak_source"] = peak_kind if roof["bound"] == "hbm" else "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"
+    src = os.path.join(ROOT, "paper_2405_14342_gb300", "csrc",
+                       "backward.cu" if dom in ("composite_bwd", "project_bwd") else "composite.cu")
+    tr = NCU_TRAFFIC.get(dom)
+    roof["traffic"] = tr["bytes"] if tr and tr.get("sha") == file_sha(src) else None
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "scene: 400x40 m strip, 0.1 m grid (1.6M surfels), C=19, 6x 960x540 surround "
+                               "pinhole cams at 1.5 m, one fwd+loss+bwd per timestep (t=8..39)",
+                   "surfels": st.n, "views_per_step": 6, "pixels_per_step": P, "classes": C,
+                   "tile": args.tile, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2: 205 MB map + 32 timesteps of targets resident, steps rotate"},
+        "roofline": roof,
+        "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof.items()},
+        "counts_per_step": {"records": round(nr), "pairs": round(K), "composited": round(E)},
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, rigs, budget_s=args.cpu_seconds)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+# --------------------------------------------------------- CPU oracle arm
+
+def oracle_step(m, cams, ex, targets_np, n_per_view, seed):
+    """Oracle fwd + loss + bwd on a pixel sample (n_per_view random pixels per view)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    pix = []
+    for v, c in enumerate(cams):
+        u = rng.integers(0, c.width, n_per_view)
+        y = rng.integers(c.height // 2, c.height, n_per_view)     # the road half of the frame
+        pix.append(np.stack([np.full(n_per_view, v), u, y], -1))
+    pix = np.ascontiguousarray(np.concatenate(pix).astype(np.int32))
+    L, g, r = oracle.loss_and_grads(m, cams, ex, targets_np, pix)
+    return len(pix), L
+
+
+def numpy_targets(cams, C, seed=3):
+    from paper_2405_14342_gb300 import scenes
+    return scenes.random_targets(cams, C, seed=seed)
+
+
+def cpu_baseline(args, rigs=None, budget_s=20.0):
+    import oracle
+    from paper_2405_14342_gb300 import scenes
+    m, field = scenes.strip_map(C=19, seed=0)
+    cams = rigs[0] if rigs else scenes.surround_rig(field, T_FIRST)
+    ex = scenes.exposure_params(6)
+    tg = numpy_targets(cams, 19)
+    t0 = time.time()
+    npx, _ = oracle_step(m, cams, ex, tg, 64, seed=0)       # calibration
+    dt = time.time() - t0
+    per = max(64, int(64 * budget_s / max(dt, 1e-3) * 0.8))
+    per = min(per, 20000)
+    t0 = time.time()
+    npx, _ = oracle_step(m, cams, ex, tg, per, seed=1)
+    dt = time.time() - t0
+    return {"value": round(npx / dt / 1e6, 6), "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{per} random road-half pixels per view x 6 views of timestep {T_FIRST} "
+                      f"(fwd+loss+bwd, FP64 brute force over all 1.6M surfels), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2405_14342_gb300 import scenes
+    m, field = scenes.strip_map(C=19, seed=0)
+    ex = scenes.exposure_params(6)
+    rigs = [scenes.surround_rig(field, T_FIRST + k) for k in range(T_COUNT)]
+    per = args.ref_pixels
+    for k in range(args.warmup):
+        oracle_step(m, rigs[k % T_COUNT], ex, numpy_targets(rigs[k % T_COUNT], 19), per, seed=k)
+    total, t0 = 0, time.time()
+    for k in range(args.steps):
+        cams = rigs[(args.warmup + k) % T_COUNT]
+        n, _ = oracle_step(m, cams, ex, numpy_targets(cams, 19), per, seed=100 + k)
+        total += n
+    dt = time.time() - t0
+    v = total / dt / 1e6
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "Mpix/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "scene: 400x40 m strip (1.6M surfels), C=19, 6x 960x540 cams; each step a "
+                                   f"sample of {per} road-half pixels per view, FP64 oracle fwd+loss+bwd"},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{per} pixels per view x 6 views per step"},
+            "e2e": {"value": round(v, 6), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--record-capacity", type=int, default=2_000_000)
+    ap.add_argument("--pair-capacity", type=int, default=12_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-pixels", type=int, default=200)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and args.steps > 2:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

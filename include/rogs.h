@@ -219,6 +219,28 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
 rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
                             int32_t key_bits, uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream);
 
+/* ------------------------------------------------------- measurement */
+
+/* Stages timed by the profiler (CUDA events on the call's stream):
+   0 cull + projection (records), 1 depth sort, 2 pair scan + emission,
+   3 tile sort + tile ranges, 4 forward compositing, 5 loss,
+   6 backward compositing, 7 projection backward. */
+#define ROGS_N_STAGES 8
+typedef struct {
+    double ms[ROGS_N_STAGES];      /* summed device time per stage */
+    uint64_t calls[ROGS_N_STAGES]; /* number of timed executions */
+} rogs_profile;
+
+/* Enable (1) or disable (0) per-stage event timing on this context and reset
+   the totals.  Timing is skipped while a stream is being captured. */
+rogs_status rogs_profile_enable(rogs_ctx* ctx, int32_t enable);
+
+/* Wait for the recorded events and return the totals since the last enable. */
+rogs_status rogs_profile_read(rogs_ctx* ctx, rogs_profile* out);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t rogs_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,15 +6,27 @@
 // axes of the perspective box cull) is done in binary32, one rounding per
 // operation, in the same order as the oracle; this file is compiled with
 // -ffp-contract=off so the host compiler cannot fuse it.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "kernels.h"
 
 using namespace rogs;
+
+namespace rogs {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace rogs
+
+struct ProfEvent {
+    int stage;
+    cudaEvent_t a, b;
+};
 
 struct rogs_ctx {
     rogs_config cfg;
@@ -35,6 +47,15 @@ struct rogs_ctx {
     ViewParams* loss_views = nullptr;
     float* poses = nullptr;
     size_t poses_cap = 0;  // floats
+    // per-stage timing
+    bool prof = false;
+    std::vector<ProfEvent> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[ROGS_N_STAGES] = {0};
+    unsigned long long prof_calls[ROGS_N_STAGES] = {0};
+    int prof_open = -1;
+    cudaEvent_t prof_open_ev = nullptr;
+    cudaStream_t prof_stream = nullptr;
 };
 
 namespace {
@@ -57,6 +78,34 @@ bool capturing(cudaStream_t s) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
     return st != cudaStreamCaptureStatusNone;
+}
+
+cudaEvent_t prof_event(rogs_ctx* ctx) {
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Close the open stage (if any) and open `stage` on stream s (-1: just close).
+void prof_mark(rogs_ctx* ctx, int stage, cudaStream_t s) {
+    if (!ctx->prof || capturing(s)) return;
+    cudaEvent_t e = prof_event(ctx);
+    cudaEventRecord(e, s);
+    if (ctx->prof_open >= 0) ctx->prof_pending.push_back({ctx->prof_open, ctx->prof_open_ev, e});
+    if (stage >= 0) {
+        cudaEvent_t e2 = prof_event(ctx);
+        cudaEventRecord(e2, s);
+        ctx->prof_open = stage;
+        ctx->prof_open_ev = e2;
+    } else {
+        ctx->prof_open = -1;
+        ctx->prof_open_ev = nullptr;
+    }
 }
 
 template <class T>
@@ -293,6 +342,12 @@ void rogs_destroy(rogs_ctx* ctx) {
                     ctx->loss_views, ctx->poses};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (const ProfEvent& pe : ctx->prof_pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    if (ctx->prof_open_ev) cudaEventDestroy(ctx->prof_open_ev);
     delete ctx;
 }
 
@@ -422,6 +477,7 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     const Consts k = make_consts(cfg);
     const SurfelPtrs sp{surfels->xyz, surfels->scale, surfels->quat, surfels->opacity, surfels->rgb, surfels->sem, n};
 
+    prof_mark(ctx, 0, s);
     upload_views(va, n_views, views, hdr, s);
     if (n > 0) {
         cull_views(views, n_views, k, sp, ctx->bits, n_words, s);
@@ -429,18 +485,23 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
         project_records(views, n_views, k, sp, ctx->bits, ctx->word_off, n_words, recs, rects, ctx->dk_a, ctx->dv_a,
                         rcap, s);
         // depth sort: stable on the binary32 depth key; ties keep (view, surfel) order
+        prof_mark(ctx, 1, s);
         radix_sort_pairs(ctx->dk_a, ctx->dv_a, ctx->dk_b, ctx->dv_b, ctx->dk_c, ctx->dv_c, &hdr->n_records, rcap, 32,
                          ctx->hist, s);
+        prof_mark(ctx, 2, s);
         scan_pairs(ctx->dv_b, rects, hdr, rcap, ctx->pair_off, ctx->pair_tiles, hdr, pcap, s);
         emit_pairs(views, ctx->dv_b, recs, rects, ctx->pair_off, hdr, rcap, ctx->pk_a, ctx->pv_a, pcap, s);
         // tile sort: stable on the global tile id; lists stay in depth order
+        prof_mark(ctx, 3, s);
         radix_sort_pairs(ctx->pk_a, ctx->pv_a, ctx->pk_b, pair_rec, ctx->pk_c, ctx->pv_c, &hdr->n_pairs, pcap,
                          bits_for(total_tiles), ctx->hist, s);
     }
     ROGS_CUDA(ctx, cudaMemsetAsync(ranges, 0, 8 * (size_t)total_tiles, s));
     if (n > 0) tile_ranges(ctx->pk_b, hdr, pcap, ranges, s);
+    prof_mark(ctx, 4, s);
     composite_fwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
                   exposure_ab, out, pix_T, pix_last, hdr, s);
+    prof_mark(ctx, -1, s);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }
@@ -459,9 +520,11 @@ rogs_status rogs_loss(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, c
     cudaStream_t s = (cudaStream_t)stream;
     rogs_status st = ensure_loss(ctx, tp, s);
     if (st != ROGS_OK) return st;
+    prof_mark(ctx, 5, s);
     upload_views(va, n_views, ctx->loss_views, nullptr, s);
     loss_fwd_bwd(ctx->loss_views, n_views, tp, ctx->cfg.num_classes, out, tgt_rgb, label, mask, lambda_c, lambda_s,
                  loss, grad_out, ctx->loss_counter, ctx->loss_partials, (int)ctx->loss_cap, s);
+    prof_mark(ctx, -1, s);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }
@@ -498,10 +561,13 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     const SurfelPtrs sp{surfels->xyz, surfels->scale, surfels->quat, surfels->opacity, surfels->rgb, surfels->sem,
                         surfels->n};
     const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
+    prof_mark(ctx, 6, s);
     composite_bwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
                   exposure_ab, grad_out, pix_T, pix_last, ctx->rec_grad, grads->exposure, s);
+    prof_mark(ctx, 7, s);
     project_bwd(views, k, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp,
                 s);
+    prof_mark(ctx, -1, s);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }
@@ -519,5 +585,40 @@ rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }
+
+rogs_status rogs_profile_enable(rogs_ctx* ctx, int32_t enable) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    rogs_profile tmp;
+    rogs_status st = rogs_profile_read(ctx, &tmp);  // drain pending events
+    ctx->prof = enable != 0;
+    for (int i = 0; i < ROGS_N_STAGES; ++i) {
+        ctx->prof_ms[i] = 0.0;
+        ctx->prof_calls[i] = 0;
+    }
+    return st;
+}
+
+rogs_status rogs_profile_read(rogs_ctx* ctx, rogs_profile* out) {
+    if (!ctx || !out) return ROGS_ERR_INVALID;
+    for (const ProfEvent& pe : ctx->prof_pending) {
+        cudaError_t e = cudaEventSynchronize(pe.b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pe.a, pe.b);
+        if (e == cudaSuccess) {
+            ctx->prof_ms[pe.stage] += ms;
+            ctx->prof_calls[pe.stage] += 1;
+        }
+        ctx->prof_pool.push_back(pe.a);
+        ctx->prof_pool.push_back(pe.b);
+    }
+    ctx->prof_pending.clear();
+    for (int i = 0; i < ROGS_N_STAGES; ++i) {
+        out->ms[i] = ctx->prof_ms[i];
+        out->calls[i] = ctx->prof_calls[i];
+    }
+    return ROGS_OK;
+}
+
+uint64_t rogs_launch_count(void) { return (uint64_t)g_launches.load(); }
 
 }  // extern "C"

@@ -249,6 +249,7 @@ static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
         composite_bwd_k<TW, TH, NCP, GP><<<grid, TW * TH, sm, s>>>(views, n_views, k, sp, recs, pair_rec,        \
                                                                    ranges, exposure_ab, grad_out, pix_T,         \
                                                                    pix_last, rec_grad, d_exposure);              \
+        note_launches(1);                                                                                        \
     } while (0)
     switch (ncp) {
         case 8: ROGS_BWD(8, 32); break;
@@ -429,6 +430,7 @@ void project_bwd(const ViewParams* views, Consts k, SurfelPtrs sp, const Record*
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     project_bwd_k<<<(int)blocks, 256, 0, s>>>(views, k, sp, recs, hdr, rec_cap, rec_grad, C, grad_channels(C), g);
+    note_launches(1);
 }
 
 }  // namespace rogs

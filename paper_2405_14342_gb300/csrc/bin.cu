@@ -37,6 +37,7 @@ void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeade
     device_exclusive_scan<RectTilesF, unsigned long long>(RectTilesF{sorted_rec, rects}, &hdr_n_records->n_records,
                                                           rec_cap, tile_sums, pair_off, &hdr->need_pairs, s);
     finalize_pairs_k<<<1, 1, 0, s>>>(hdr, pair_cap);
+    note_launches(1);
 }
 
 __global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict__ views,
@@ -75,6 +76,7 @@ void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Recor
     if (blocks < 1) blocks = 1;
     emit_pairs_k<<<(int)blocks, 256, 0, s>>>(views, sorted_rec, recs, rects, pair_off, hdr, rec_cap, pair_keys,
                                               pair_vals, pair_cap);
+    note_launches(1);
 }
 
 __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict__ keys,
@@ -95,6 +97,7 @@ void tile_ranges(const uint32_t* sorted_tile, const StateHeader* hdr, unsigned l
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
     tile_ranges_k<<<(int)blocks, 256, 0, s>>>(sorted_tile, hdr, pair_cap, ranges);
+    note_launches(1);
 }
 
 }  // namespace rogs

@@ -170,6 +170,7 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
         }                                                                                                      \
         composite_fwd_k<TW, TH, NCP><<<grid, TW * TH, sm, s>>>(views, n_views, k, sp, recs, pair_rec, ranges, \
                                                                exposure_ab, out, pix_T, pix_last, hdr);       \
+        note_launches(1);                                                                                      \
     } while (0)
     switch (ncp) {
         case 8: ROGS_FWD(8); break;

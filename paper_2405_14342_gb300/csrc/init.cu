@@ -89,6 +89,7 @@ void init_from_poses(const float* grid_xy, long long n, const float* poses_dev, 
     const long long blocks = (n + kInitThreads - 1) / kInitThreads;
     init_k<<<(unsigned)blocks, kInitThreads, 0, s>>>(grid_xy, n, poses_dev, n_poses, exact_plane, out_z, out_quat,
                                                      out_nearest);
+    note_launches(1);
 }
 
 }  // namespace rogs

@@ -10,6 +10,9 @@
 
 namespace rogs {
 
+// Count kernel launches made by this library (reported by rogs_launch_count).
+void note_launches(int n);
+
 struct SurfelPtrs {
     const float *xyz, *scale, *quat, *opacity, *rgb, *sem;
     long long n;

@@ -133,6 +133,7 @@ void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, 
     loss_k<<<nb > 0 ? nb : 1, kLossThreads, 0, s>>>(views, n_views, total_pixels, C, out, tgt_rgb, label, mask,
                                                     lambda_c, lambda_s, counter, grad_out, partials);
     loss_final_k<<<1, 256, 0, s>>>(partials, nb, counter, loss);
+    note_launches(3);
     (void)n_blocks_cap;
 }
 

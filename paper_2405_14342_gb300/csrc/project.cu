@@ -223,6 +223,7 @@ __global__ void upload_views_k(ViewsArg va, int n_views, ViewParams* dst, StateH
 
 void upload_views(const ViewsArg& va, int n_views, ViewParams* dst, StateHeader* hdr, cudaStream_t s) {
     upload_views_k<<<1, 256, 0, s>>>(va, n_views, dst, hdr);
+    note_launches(1);
 }
 
 static int grid_for_words(long long n_words) {
@@ -236,6 +237,7 @@ void cull_views(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, u
                 cudaStream_t s) {
     size_t sm = sizeof(ViewParams) * (size_t)n_views;
     cull_k<<<grid_for_words(n_words), kProjThreads, sm, s>>>(views, n_views, k, sp, bits, n_words);
+    note_launches(1);
 }
 
 struct PopcF {
@@ -256,10 +258,12 @@ void scan_visible(const uint32_t* bits, long long n_words_total, uint32_t* word_
     device_exclusive_scan<PopcF, uint32_t>(PopcF{bits}, nullptr, (unsigned long long)n_words_total, tile_sums,
                                            word_off, &hdr->need_records, s);
     finalize_records_k<<<1, 1, 0, s>>>(hdr, rec_cap);
+    note_launches(1);
 }
 
 void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s) {
     finalize_records_k<<<1, 1, 0, s>>>(hdr, rec_cap);
+    note_launches(1);
 }
 
 void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, const uint32_t* bits,
@@ -268,6 +272,7 @@ void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs 
     size_t sm = sizeof(ViewParams) * (size_t)n_views;
     project_k<<<grid_for_words(n_words), kProjThreads, sm, s>>>(views, n_views, k, sp, bits, word_off, n_words, recs,
                                                                 rects, keys, vals, rec_cap);
+    note_launches(1);
 }
 
 }  // namespace rogs

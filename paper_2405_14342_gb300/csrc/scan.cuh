@@ -130,6 +130,7 @@ inline void device_exclusive_scan(F f, const unsigned long long* n_ptr, unsigned
     scan_reduce_k<F, T><<<nt, kScanThreads, 0, s>>>(f, n_ptr, cap, tile_sums);
     scan_tiles_k<T><<<1, kScanThreads, 0, s>>>(tile_sums, nt, total);
     scan_down_k<F, T><<<nt, kScanThreads, 0, s>>>(f, n_ptr, cap, tile_sums, out);
+    note_launches(3);
 }
 
 }  // namespace rogs

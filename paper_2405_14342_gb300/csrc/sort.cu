@@ -181,6 +181,7 @@ void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
     int grid = (int)(tiles < 1 ? 1 : (tiles > 2048 ? 2048 : tiles));
     if (passes == 0) {
         copy_pairs_k<<<grid, 256, 0, s>>>(kin, vin, kout, vout, n_ptr, cap);
+        note_launches(1);
         return;
     }
     const uint32_t* sk = kin;
@@ -196,6 +197,7 @@ void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
         rs_upsweep_k<<<grid, kRsThreads, 0, s>>>(sk, n_ptr, cap, shift, mask, hist);
         rs_rowscan_k<<<256, kScanThreads, 0, s>>>(hist, n_ptr, cap, row_total);
         rs_downsweep_k<<<grid, kRsThreads, 0, s>>>(sk, sv, dk, dv, n_ptr, cap, shift, mask, hist, row_total);
+        note_launches(3);
         sk = dk;
         sv = dv;
     }

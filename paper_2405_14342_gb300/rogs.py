@@ -67,6 +67,13 @@ class rogs_state_layout(C.Structure):
                 ("total_pixels", C.c_int64)]
 
 
+class rogs_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("calls", C.c_uint64 * 8)]
+
+
+STAGES = ("cull_project", "depth_sort", "pair_emit", "tile_sort", "composite_fwd", "loss", "composite_bwd",
+          "project_bwd")
+
 _lib = None
 
 
@@ -96,7 +103,11 @@ def lib():
         L.rogs_render_bwd.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
                                       P, P, C.POINTER(rogs_grads), P]
         L.rogs_sort_pairs.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P, P]
-        for name in ("rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
+        L.rogs_profile_enable.argtypes = [P, C.c_int32]
+        L.rogs_profile_read.argtypes = [P, C.POINTER(rogs_profile)]
+        L.rogs_launch_count.argtypes = []
+        L.rogs_launch_count.restype = C.c_uint64
+        for name in ("rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
                      "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
                      "rogs_render_bwd", "rogs_sort_pairs"):
             getattr(L, name).restype = S
@@ -220,3 +231,17 @@ def rogs_render_bwd(ctx, surf: rogs_surfels, cam_arr, n_views, exposure_ab, stat
 def rogs_sort_pairs(ctx, keys_in, vals_in, key_bits, keys_out, vals_out, stream=None):
     _check(ctx, lib().rogs_sort_pairs(ctx, _ptr(keys_in), _ptr(vals_in), int(keys_in.numel()), int(key_bits),
                                       _ptr(keys_out), _ptr(vals_out), _stream(stream)))
+
+
+def rogs_profile_enable(ctx, enable=True):
+    _check(ctx, lib().rogs_profile_enable(ctx, int(bool(enable))))
+
+
+def rogs_profile_read(ctx) -> dict:
+    p = rogs_profile()
+    _check(ctx, lib().rogs_profile_read(ctx, C.byref(p)))
+    return {name: (float(p.ms[i]), int(p.calls[i])) for i, name in enumerate(STAGES)}
+
+
+def rogs_launch_count() -> int:
+    return int(lib().rogs_launch_count())
