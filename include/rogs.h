@@ -219,6 +219,33 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
 rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
                             int32_t key_bits, uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream);
 
+/* Largest n accepted by rogs_sort_pairs_noalloc. */
+#define ROGS_NOALLOC_MAX_PAIRS 1048576
+
+/* rogs_sort_pairs without a context and without any device allocation (the
+   paper has no counterpart; this is a library service).  It exists for
+   callers that cannot allocate device memory where they sort -- code that
+   enqueues into a stream of a host framework which has reserved all device
+   memory itself, loops that forbid allocator calls, plugin hooks that run
+   while another component owns the allocator -- and so cannot create a
+   rogs_ctx.  Same result as rogs_sort_pairs: stable LSD radix sort of
+   (key, value) pairs on key bits [0, key_bits); all pointers device; inputs
+   are not modified; keys_out/vals_out must not overlap the inputs.
+   Scratch: a fixed array of 2 * ROGS_NOALLOC_MAX_PAIRS + 65792 uint32
+   (about 8.65 MB) compiled into the library's device image; every GPU that
+   loads the library holds it until the process exits.  The first call on a
+   device looks the array's device address up (cudaGetSymbolAddress) and
+   caches it: make that first call before any stream capture on that device.
+   All calls share the one array, so calls whose executions overlap on the
+   GPU (different streams, or concurrent host threads) race and corrupt each
+   other's results; serialise them.  Nothing in the array needs clearing
+   between calls.  Errors: ROGS_ERR_CAPACITY if n > ROGS_NOALLOC_MAX_PAIRS,
+   ROGS_ERR_INVALID for n < 0, key_bits outside [0, 32] or a NULL pointer
+   with n > 0, ROGS_ERR_CUDA if the address lookup or a launch fails.  The
+   current device must be the device of `stream`. */
+rogs_status rogs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int32_t key_bits,
+                                    uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream);
+
 /* ------------------------------------------------------- measurement */
 
 /* Stages timed by the profiler (CUDA events on the call's stream):
