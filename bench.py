@@ -107,11 +107,11 @@ class ClockSampler:
 
 # --------------------------------------------------------------- workload
 
-def build_workload(rank: int, C: int, world: int):
+def build_workload(rank: int, C: int, world: int, n_t: int):
     from paper_2405_14342_gb300 import scenes
     m, field = scenes.strip_map(C=C, seed=0)
     t0 = T_FIRST + 40 * rank          # each rank takes its own stretch of road (weak scaling)
-    rigs = [scenes.surround_rig(field, t0 + k) for k in range(T_COUNT)]
+    rigs = [scenes.surround_rig(field, t0 + k) for k in range(n_t)]
     return m, field, rigs
 
 
@@ -154,7 +154,8 @@ def run_ours(args):
 
     C = 19
     tile = tuple(int(x) for x in args.tile.split("x"))
-    m, field, rigs = build_workload(rank, C, world)
+    n_t = args.timesteps
+    m, field, rigs = build_workload(rank, C, world, n_t)
     exposure = torch.as_tensor(scenes.exposure_params(6), device="cuda")
     rr = R.Renderer(C, record_capacity=args.record_capacity, pair_capacity=args.pair_capacity, tile=tile)
     rr.reserve(m.n, 6)
@@ -168,14 +169,14 @@ def run_ours(args):
     gout = torch.empty_like(frames[0].out)
 
     def step(k):
-        fr = frames[k % T_COUNT]
-        trgb, lab, msk = targets[k % T_COUNT]
+        fr = frames[k % n_t]
+        trgb, lab, msk = targets[k % n_t]
         rr.forward(st, fr, exposure)
         rr.loss(fr, trgb, lab, msk, 1.0, 0.06, loss=loss, grad_out=gout)
         rr.backward(st, fr, exposure, gout, grads=grads)
 
     # set-up: every timestep's forward must fit the capacities (raises otherwise)
-    for k in range(T_COUNT):
+    for k in range(n_t):
         rr.forward(st, frames[k], exposure)
     torch.cuda.synchronize()
     for fr in frames:
@@ -214,7 +215,7 @@ def run_ours(args):
     # per-step counts of the timed steps (deterministic per timestep)
     comp, nrec, npair = 0, 0, 0
     for k in range(args.steps):
-        c = rr.counts(frames[(args.warmup + k) % T_COUNT])
+        c = rr.counts(frames[(args.warmup + k) % n_t])
         comp += c.composited
         nrec += c.n_records
         npair += c.n_pairs
@@ -223,7 +224,7 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         pinned = []
-        for k in range(min(8, T_COUNT)):
+        for k in range(min(8, n_t)):
             a, b, c = targets[k]
             pinned.append((a.cpu().pin_memory(), b.cpu().pin_memory(), c.cpu().pin_memory()))
         dev = [torch.empty_like(x) for x in targets[0]]
@@ -306,7 +307,9 @@ def run_ours(args):
                                "pinhole cams at 1.5 m, one fwd+loss+bwd per timestep (t=8..39)",
                    "surfels": st.n, "views_per_step": 6, "pixels_per_step": P, "classes": C,
                    "tile": args.tile, "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "inputs larger than L2: 205 MB map + 32 timesteps of targets resident, steps rotate"},
+                   "timesteps_resident": n_t,
+                   "l2": f"inputs larger than L2: 205 MB map + {n_t} timesteps of targets/outputs resident, "
+                         "steps rotate"},
         "roofline": roof,
         "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof.items()},
         "counts_per_step": {"records": round(nr), "pairs": round(K), "composited": round(E)},
@@ -404,6 +407,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-pixels", type=int, default=200)
+    ap.add_argument("--timesteps", type=int, default=T_COUNT, help="timesteps kept resident (profiling: fewer)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and args.steps > 2:
         args.warmup = 3

@@ -50,20 +50,8 @@ __device__ __forceinline__ void stage_entry_bwd(const Record* __restrict__ recs,
         if (ch > 3 + C) f[ch] = 0.0f;
 }
 
-// Transposing butterfly over 32 values: on return v[0] of lane l holds the
-// sum over the warp of every lane's v[l].
-__device__ __forceinline__ void transpose_reduce32(float (&v)[32], int lane) {
-#pragma unroll
-    for (int h = 16; h >= 1; h >>= 1) {
-        const bool up = (lane & h) != 0;
-#pragma unroll
-        for (int i = 0; i < h; ++i) {
-            const float send = up ? v[i] : v[i + h];
-            const float keep = up ? v[i + h] : v[i];
-            v[i] = keep + __shfl_xor_sync(kFull, send, h);
-        }
-    }
-}
+constexpr int kBwdChunk = 64;    // entries staged per block iteration
+constexpr int kSubPad = 33;      // padded row stride of the per-warp sub-chunk tables
 
 template <int TW, int TH, int NCP, int GP>
 __global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __restrict__ views, int n_views, Consts k,
@@ -78,12 +66,19 @@ __global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __r
     constexpr int BLK = TW * TH;
     constexpr int WX = TW / 8;
     constexpr int NW = BLK / 32;
+    constexpr int CH = BLK < kBwdChunk ? BLK : kBwdChunk;
+    constexpr int GPS = GP + 1;
+    constexpr int SP = kSubPad;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     extern __shared__ float4 smem_bwd[];
     float4* s_m = smem_bwd;
-    float4* s_c = s_m + BLK;
-    float* s_f = reinterpret_cast<float*>(s_c + BLK);
-    float* s_g = s_f + BLK * NCP;
-    uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_g + BLK * GP);
+    float4* s_c = s_m + CH;
+    float* s_f = reinterpret_cast<float*>(s_c + CH);
+    uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_f + CH * NCP);
+    float* s_g = reinterpret_cast<float*>(s_rec + CH);
+    float* s_G = s_g + CH * GPS + warp * ((NCP + 2 * 32) * SP);   // this warp's tables
+    float* s_w = s_G + NCP * SP;
+    float* s_p = s_w + 32 * SP;
     __shared__ uint32_t s_maxlast;
     __shared__ float s_exp[NW][2];
 
@@ -93,9 +88,9 @@ __global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __r
     const int W = v.W, H = v.H;
     const long long lt = tile - v.tile_base;
     const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = tx * TW + (warp % WX) * 8 + (lane & 7);
-    const int py = ty * TH + (warp / WX) * 4 + (lane >> 3);
+    const int wx0 = tx * TW + (warp % WX) * 8, wy0 = ty * TH + (warp / WX) * 4;
+    const int px = wx0 + (lane & 7);
+    const int py = wy0 + (lane >> 3);
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     const uint2 rg = ranges[tile];
@@ -107,9 +102,9 @@ __global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __r
 
     float T = 1.0f;
     uint32_t last = 0;
-    float G[NCP], S[NCP];
+    float G[NCP];
 #pragma unroll
-    for (int ch = 0; ch < NCP; ++ch) { G[ch] = 0.0f; S[ch] = 0.0f; }
+    for (int ch = 0; ch < NCP; ++ch) G[ch] = 0.0f;
     float gsum_rgb = 0.0f;
     if (inside) {
         const long long pix = v.pix_base + (long long)py * W + px;
@@ -123,94 +118,128 @@ __global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __r
         T = pix_T[pix];
         last = pix_last[pix];
     }
+#pragma unroll
+    for (int ch = 0; ch < NCP; ++ch) s_G[ch * SP + lane] = G[ch];
+    const uint32_t wmax = __reduce_max_sync(kFull, last);
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
-    if (last) atomicMax(&s_maxlast, last);
+    if (lane == 0 && wmax) atomicMax(&s_maxlast, wmax);
     __syncthreads();
     const uint32_t maxlast = s_maxlast;
 
+    // Scalar suffix: G . S_k with S_k = sum_{j>k} w_j f_j equals sum_{j>k} w_j (G . f_j),
+    // so one float per pixel replaces the per-channel suffix sums.
+    float Ssum = 0.0f;
+    float cr0 = 0.0f, cr1 = 0.0f, cr2 = 0.0f;   // raw rgb (before exposure) for dL/da of Eq. 7
+
     for (uint32_t cend = maxlast; cend > 0;) {
-        const uint32_t cbeg = cend > (uint32_t)BLK ? cend - BLK : 0u;
+        const uint32_t cbeg = cend > (uint32_t)CH ? cend - CH : 0u;
         const int cnt = (int)(cend - cbeg);
         if (threadIdx.x < cnt)
             stage_entry_bwd<NCP>(recs, pair_rec[start + cbeg + threadIdx.x], sp, C, s_m, s_c, s_f, s_rec, threadIdx.x);
-        for (int q = threadIdx.x; q < cnt * GP; q += BLK) s_g[q] = 0.0f;
+        for (int q = threadIdx.x; q < cnt * GPS; q += BLK) s_g[q] = 0.0f;
         __syncthreads();
-        for (int jj = cnt - 1; jj >= 0; --jj) {
-            const uint32_t jl = cbeg + (uint32_t)jj;  // index in the tile list
-            float gv[GP];
+        for (int sb = cnt; sb > 0; sb -= 32) {
+            const int s0 = sb > 32 ? sb - 32 : 0;
+            if (cbeg + (uint32_t)s0 >= wmax) continue;   // no pixel of this warp reaches these entries
+            // phase A (lane = pixel): reverse recursion over the sub-chunk
+            for (int jj = sb - 1; jj >= s0; --jj) {
+                float w = 0.0f, dpw = 0.0f;
+                if (cbeg + (uint32_t)jj < last) {
+                    const float4 m = s_m[jj];
+                    const float4 c = s_c[jj];
+                    const float dx = pix_offset(pxc, m.x, m.z);
+                    const float dy = pix_offset(pyc, m.y, m.w);
+                    float g;
+                    const float a = surfel_alpha(dx, dy, c.x, c.y, c.z, c.w, amax, g);
+                    if (a >= amin) {
+                        const float oma = __fsub_rn(1.0f, a);
+                        T = __fdiv_rn(T, oma);   // T_k
+                        w = a * T;
+                        const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
+                        float D = 0.0f;
 #pragma unroll
-            for (int q = 0; q < GP; ++q) gv[q] = 0.0f;
-            bool contrib = false;
-            if (jl < last) {
-                const float4 m = s_m[jj];
-                const float4 c = s_c[jj];
-                const float dx = pix_offset(pxc, m.x, m.z);
-                const float dy = pix_offset(pyc, m.y, m.w);
-                float g;
-                const float a = surfel_alpha(dx, dy, c.x, c.y, c.z, c.w, amax, g);
-                if (a >= amin) {
-                    contrib = true;
-                    const float oma = __fsub_rn(1.0f, a);
-                    T = __fdiv_rn(T, oma);           // T_k
-                    const float w = a * T;
-                    const float ioma = 1.0f / oma;
-                    const float* f = s_f + jj * NCP;
-                    float da = 0.0f;
-#pragma unroll
-                    for (int ch = 0; ch < NCP; ++ch) {
-                        const float fc = f[ch];
-                        if (6 + ch < GP) gv[6 + ch] = w * G[ch];
-                        da = fmaf(G[ch], fmaf(T, fc, -S[ch] * ioma), da);
-                        S[ch] = fmaf(w, fc, S[ch]);
-                    }
-                    const float ag = c.w * g;
-                    if (ag < amax) {
-                        const float dpow = da * ag;
-                        gv[0] = dpow * (c.x * dx + c.y * dy);
-                        gv[1] = dpow * (c.y * dx + c.z * dy);
-                        gv[2] = -0.5f * dpow * dx * dx;
-                        gv[3] = -dpow * dx * dy;
-                        gv[4] = -0.5f * dpow * dy * dy;
-                        gv[5] = da * g;
+                        for (int q = 0; q < NCP / 4; ++q) {
+                            const float4 f = f4[q];
+                            D = fmaf(G[4 * q], f.x, D);
+                            D = fmaf(G[4 * q + 1], f.y, D);
+                            D = fmaf(G[4 * q + 2], f.z, D);
+                            D = fmaf(G[4 * q + 3], f.w, D);
+                        }
+                        const float da = fmaf(T, D, -Ssum / oma);
+                        Ssum = fmaf(w, D, Ssum);
+                        const float4 f0 = f4[0];
+                        cr0 = fmaf(w, f0.x, cr0);
+                        cr1 = fmaf(w, f0.y, cr1);
+                        cr2 = fmaf(w, f0.z, cr2);
+                        const float ag = c.w * g;
+                        if (ag < amax) dpw = da * ag;   // d alpha = dpw / alpha
                     }
                 }
+                const int r = jj - s0;
+                s_w[r * SP + lane] = w;
+                s_p[r * SP + lane] = dpw;
             }
-            if (__any_sync(kFull, contrib)) {
-                if (GP == 32) {
-                    float r[32];
+            __syncwarp();
+            // phase B (lane = entry): reduce the entry's gradient over the warp's 32 pixels
+            if (lane < sb - s0) {
+                const int e = s0 + lane;
+                const float4 m = s_m[e];
+                const float4 c = s_c[e];
+                float acc[NCP];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) r[q] = gv[q];
-                    transpose_reduce32(r, lane);
-                    if (r[0] != 0.0f) atomicAdd(&s_g[jj * GP + lane], r[0]);
-                } else {
-                    float r[32];
+                for (int ch = 0; ch < NCP; ++ch) acc[ch] = 0.0f;
+                float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, g3 = 0.0f, g4 = 0.0f, g5 = 0.0f;
+                bool any = false;
+                const float* rw = s_w + lane * SP;
+                const float* rp = s_p + lane * SP;
+                for (int p = 0; p < 32; ++p) {
+                    const float w = rw[p];
+                    if (w != 0.0f) {
+                        any = true;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) r[q] = gv[q];
-                    transpose_reduce32(r, lane);
-                    if (r[0] != 0.0f) atomicAdd(&s_g[jj * GP + lane], r[0]);
+                        for (int ch = 0; ch < NCP; ++ch) acc[ch] = fmaf(w, s_G[ch * SP + p], acc[ch]);
+                        const float dpw = rp[p];
+                        const float dx = pix_offset((float)(wx0 + (p & 7)) + 0.5f, m.x, m.z);
+                        const float dy = pix_offset((float)(wy0 + (p >> 3)) + 0.5f, m.y, m.w);
+                        g0 = fmaf(dpw, c.x * dx + c.y * dy, g0);
+                        g1 = fmaf(dpw, c.y * dx + c.z * dy, g1);
+                        g2 = fmaf(-0.5f * dpw, dx * dx, g2);
+                        g3 = fmaf(-dpw, dx * dy, g3);
+                        g4 = fmaf(-0.5f * dpw, dy * dy, g4);
+                        g5 += dpw;
+                    }
+                }
+                if (any) {
+                    float* dst = s_g + e * GPS;
+                    atomicAdd(dst + 0, g0);
+                    atomicAdd(dst + 1, g1);
+                    atomicAdd(dst + 2, g2);
+                    atomicAdd(dst + 3, g3);
+                    atomicAdd(dst + 4, g4);
+                    atomicAdd(dst + 5, g5 / c.w);
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) r[q] = gv[(32 + q) % GP];
-                    transpose_reduce32(r, lane);
-                    if (r[0] != 0.0f) atomicAdd(&s_g[jj * GP + 32 + lane], r[0]);
+                    for (int ch = 0; ch < NCP; ++ch)
+                        if (ch < nch && 6 + ch < GP) atomicAdd(dst + 6 + ch, acc[ch]);
                 }
             }
+            __syncwarp();
         }
         __syncthreads();
         for (int q = threadIdx.x; q < cnt * GP; q += BLK) {
-            const float val = s_g[q];
-            if (val != 0.0f) atomicAdd(&rec_grad[(unsigned long long)s_rec[q / GP] * GP + (q % GP)], val);
+            const int e = q / GP, ch = q - e * GP;
+            const float val = s_g[e * GPS + ch];
+            if (val != 0.0f) atomicAdd(&rec_grad[(unsigned long long)s_rec[e] * GP + ch], val);
         }
         __syncthreads();
         cend = cbeg;
     }
 
-    // exposure (Eq. 7): dL/db = sum g', dL/da = sum g' e^a c_raw, c_raw = S_rgb
+    // exposure (Eq. 7): dL/db = sum g', dL/da = sum g' e^a c_raw
     float e_a = 0.0f, e_b = 0.0f;
     if (inside) {
         e_b = gsum_rgb;
-        // G[0..2] already hold e^a g'; c_raw = S[0..2]
-        e_a = G[0] * S[0] + G[1] * S[1] + G[2] * S[2];
+        e_a = G[0] * cr0 + G[1] * cr1 + G[2] * cr2;   // G[0..2] hold e^a g'
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -228,7 +257,10 @@ __global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __r
 }
 
 static size_t bwd_smem_bytes(int blk, int ncp, int gp) {
-    return (size_t)blk * (32 + 4 * (size_t)ncp + 4 * (size_t)gp + 4);
+    const size_t ch = blk < kBwdChunk ? blk : kBwdChunk;
+    const size_t staged = ch * (32 + 4 * (size_t)ncp + 4 + 4 * (size_t)(gp + 1));
+    const size_t per_warp = 4 * (size_t)(ncp + 2 * 32) * kSubPad;
+    return staged + (size_t)(blk / 32) * per_warp;
 }
 
 template <int TW, int TH>

@@ -104,11 +104,19 @@ __global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restr
     }
 }
 
-__global__ void loss_final_k(const float* __restrict__ partials, int n, const unsigned long long* __restrict__ counter,
-                             float* __restrict__ loss) {
-    __shared__ double sh[256];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)partials[i];
+// FP64 is slow on this part, so the partials are summed in FP32 with Kahan
+// compensation per thread and a fixed-order tree across threads.
+__global__ void __launch_bounds__(256) loss_final_k(const float* __restrict__ partials, int n,
+                                                    const unsigned long long* __restrict__ counter,
+                                                    float* __restrict__ loss) {
+    __shared__ float sh[256];
+    float s = 0.0f, comp = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float y = partials[i] - comp;
+        const float t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    }
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -117,7 +125,7 @@ __global__ void loss_final_k(const float* __restrict__ partials, int n, const un
     }
     if (threadIdx.x == 0) {
         const unsigned long long nm = *counter;
-        loss[0] = nm ? (float)(sh[0] / (double)nm) : 0.0f;
+        loss[0] = nm ? sh[0] / (float)nm : 0.0f;
     }
 }
 
