@@ -1,18 +1,19 @@
 // backward.cu -- stage 4: reverse-order backward of the compositing and the
 // projection (the adjoint of RoGs Eqs. 2, 5, 6, 7; not written in the paper).
 //
-// composite_bwd_k: one CTA per tile.  Each pixel starts from its final
-// transmittance T and walks its tile list backwards from its last composited
-// entry, recovering T_k = T_{k+1} / (1 - a_k) and carrying the suffix sum
-// S_k = sum_{j>k} w_j f_j, so that
-//     dout/df_k = w_k,   dout/da_k = T_k f_k - S_k / (1 - a_k)
-// need no per-pixel list.  The chunk of entries is re-staged in shared memory
-// exactly as in the forward and a_k is recomputed with the same function, so
-// the same entries contribute.  Each warp reduces an entry's gradient vector
-// (mean 2, conic 3, alpha 1, features 3 + C + 1) across its 32 pixels with a
-// transposing butterfly (31 shuffles leave lane c holding the warp sum of
-// channel c), adds it into a per-chunk shared-memory accumulator, and the CTA
-// flushes the chunk with one global atomic per non-zero (entry, channel).
+// composite_bwd_k: each warp owns an 8x4 pixel block of a tile and walks the
+// tile's list backwards from the largest last-composited index of its pixels,
+// 32 entries at a time, keeping only the entries whose footprint can reach its
+// block.  For every pixel it recovers T_k = T_{k+1} / (1 - a_k) and carries one
+// scalar suffix sum, S_k = sum_{j>k} w_j (G . f_j) with G = dL/dout at the
+// pixel, which gives dL/da_k = T_k (G . f_k) - S_k / (1 - a_k) without a
+// per-pixel list and without per-channel suffix sums (phase A, lane = pixel).
+// The per-(entry, pixel) weights and dL/dpower go to a small shared-memory
+// table; then each lane takes one entry and sums its gradient (mean 2, conic
+// 3, alpha 1, features 3 + C + 1) over the warp's pixels that received
+// anything (phase B, lane = entry), and the warp adds each entry's row to the
+// per-record gradient buffer with one coalesced atomic per channel.  Warps run
+// independently (no block barrier); a block holds two warps of one tile.
 //
 // project_bwd_k: one thread per record; chains the 2D gradients through the
 // conic inverse, Sigma' = T2 T2^T + eps I, T2 = J W M, the perspective
@@ -27,78 +28,66 @@ namespace rogs {
 int grad_channels(int C) { return padded_channels(C) <= 24 ? 32 : 64; }
 
 template <int NCP>
-__device__ __forceinline__ void stage_entry_bwd(const Record* __restrict__ recs, const uint32_t rec,
-                                                const SurfelPtrs& sp, int C, float4* s_m, float4* s_c, float* s_f,
-                                                uint32_t* s_rec, int slot) {
-    const float4* r4 = reinterpret_cast<const float4*>(recs + rec);
-    const float4 a = r4[0];
-    const float4 b = r4[1];
-    const float4 c = r4[2];
-    s_m[slot] = a;
-    s_c[slot] = b;
-    s_rec[slot] = rec;
-    const uint32_t s = __float_as_uint(c.z);
-    float* f = s_f + slot * NCP;
+__device__ __forceinline__ void stage_features_bwd(float* f, uint32_t s, float depth, const SurfelPtrs& sp, int C) {
     f[0] = sp.rgb[3ull * s];
     f[1] = sp.rgb[3ull * s + 1];
     f[2] = sp.rgb[3ull * s + 2];
     const float* sem = sp.sem + (unsigned long long)C * s;
     for (int ch = 0; ch < C; ++ch) f[3 + ch] = sem[ch];
-    f[3 + C] = c.x;
+    f[3 + C] = depth;
 #pragma unroll
     for (int ch = 0; ch < NCP; ++ch)
         if (ch > 3 + C) f[ch] = 0.0f;
 }
 
-constexpr int kBwdChunk = 64;    // entries staged per block iteration
-constexpr int kSubPad = 33;      // padded row stride of the per-warp sub-chunk tables
+constexpr int kSubPad = 33;   // padded row stride of the per-warp tables
+constexpr int kBwdWarpsPerBlock = 2;
+
+template <int NCP>
+__host__ __device__ constexpr int bwd_warp_floats() {
+    return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 32 + 2 * 32 * kSubPad + NCP * kSubPad;
+}
 
 template <int TW, int TH, int NCP, int GP>
-__global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __restrict__ views, int n_views, Consts k,
-                                                           SurfelPtrs sp, const Record* __restrict__ recs,
-                                                           const uint32_t* __restrict__ pair_rec,
-                                                           const uint2* __restrict__ ranges,
-                                                           const float* __restrict__ exposure_ab,
-                                                           const float* __restrict__ grad_out,
-                                                           const float* __restrict__ pix_T,
-                                                           const uint32_t* __restrict__ pix_last,
-                                                           float* __restrict__ rec_grad, float* __restrict__ d_exposure) {
-    constexpr int BLK = TW * TH;
+__global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
+    const ViewParams* __restrict__ views, int n_views, Consts k, SurfelPtrs sp, const Record* __restrict__ recs,
+    const uint32_t* __restrict__ pair_rec, const uint2* __restrict__ ranges, const float* __restrict__ exposure_ab,
+    const float* __restrict__ grad_out, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
+    float* __restrict__ rec_grad, float* __restrict__ d_exposure) {
     constexpr int WX = TW / 8;
-    constexpr int NW = BLK / 32;
-    constexpr int CH = BLK < kBwdChunk ? BLK : kBwdChunk;
-    constexpr int GPS = GP + 1;
+    constexpr int NW = TW * TH / 32;
+    constexpr int GROUPS = NW / kBwdWarpsPerBlock;
     constexpr int SP = kSubPad;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const long long tile = blockIdx.x / GROUPS;
+    const int warp = (int)(blockIdx.x % GROUPS) * kBwdWarpsPerBlock + wib;   // warp index inside the tile
     extern __shared__ float4 smem_bwd[];
-    float4* s_m = smem_bwd;
-    float4* s_c = s_m + CH;
-    float* s_f = reinterpret_cast<float*>(s_c + CH);
-    uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_f + CH * NCP);
-    float* s_g = reinterpret_cast<float*>(s_rec + CH);
-    float* s_G = s_g + CH * GPS + warp * ((NCP + 2 * 32) * SP);   // this warp's tables
-    float* s_w = s_G + NCP * SP;
+    float* wbase = reinterpret_cast<float*>(smem_bwd) + wib * bwd_warp_floats<NCP>();
+    float4* s_m = reinterpret_cast<float4*>(wbase);
+    float4* s_c = s_m + 32;
+    float* s_f = reinterpret_cast<float*>(s_c + 32);
+    uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_f + 32 * NCP);
+    uint32_t* s_idx = s_rec + 32;
+    float* s_w = reinterpret_cast<float*>(s_idx + 32);
     float* s_p = s_w + 32 * SP;
-    __shared__ uint32_t s_maxlast;
-    __shared__ float s_exp[NW][2];
+    float* s_G = s_p + 32 * SP;
 
-    const long long tile = blockIdx.x;
     const int vi = view_of_tile(views, n_views, tile);
     const ViewParams& v = views[vi];
     const int W = v.W, H = v.H;
     const long long lt = tile - v.tile_base;
     const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
-    const int wx0 = tx * TW + (warp % WX) * 8, wy0 = ty * TH + (warp / WX) * 4;
-    const int px = wx0 + (lane & 7);
-    const int py = wy0 + (lane >> 3);
+    const int bx = tx * TW + (warp % WX) * 8, by = ty * TH + (warp / WX) * 4;
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-    const uint2 rg = ranges[tile];
-    const uint32_t start = rg.x;
+    const uint32_t start = ranges[tile].x;
     const int C = k.C;
     const int nch = 3 + C + 1;
     const float amin = k.alpha_min, amax = k.alpha_max;
     const float ea = expf(exposure_ab[2 * v.exp_idx]);
+    const unsigned lt_mask = lanemask_lt();
 
     float T = 1.0f;
     uint32_t last = 0;
@@ -121,118 +110,129 @@ __global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __r
 #pragma unroll
     for (int ch = 0; ch < NCP; ++ch) s_G[ch * SP + lane] = G[ch];
     const uint32_t wmax = __reduce_max_sync(kFull, last);
-    if (threadIdx.x == 0) s_maxlast = 0;
-    __syncthreads();
-    if (lane == 0 && wmax) atomicMax(&s_maxlast, wmax);
-    __syncthreads();
-    const uint32_t maxlast = s_maxlast;
+    __syncwarp();
 
-    // Scalar suffix: G . S_k with S_k = sum_{j>k} w_j f_j equals sum_{j>k} w_j (G . f_j),
-    // so one float per pixel replaces the per-channel suffix sums.
-    float Ssum = 0.0f;
-    float cr0 = 0.0f, cr1 = 0.0f, cr2 = 0.0f;   // raw rgb (before exposure) for dL/da of Eq. 7
+    float Ssum = 0.0f;                          // sum_{j>k} w_j (G . f_j)
+    float cr0 = 0.0f, cr1 = 0.0f, cr2 = 0.0f;   // raw rgb, for dL/da of Eq. 7
 
-    for (uint32_t cend = maxlast; cend > 0;) {
-        const uint32_t cbeg = cend > (uint32_t)CH ? cend - CH : 0u;
-        const int cnt = (int)(cend - cbeg);
-        if (threadIdx.x < cnt)
-            stage_entry_bwd<NCP>(recs, pair_rec[start + cbeg + threadIdx.x], sp, C, s_m, s_c, s_f, s_rec, threadIdx.x);
-        for (int q = threadIdx.x; q < cnt * GPS; q += BLK) s_g[q] = 0.0f;
-        __syncthreads();
-        for (int sb = cnt; sb > 0; sb -= 32) {
-            const int s0 = sb > 32 ? sb - 32 : 0;
-            if (cbeg + (uint32_t)s0 >= wmax) continue;   // no pixel of this warp reaches these entries
-            // phase A (lane = pixel): reverse recursion over the sub-chunk
-            for (int jj = sb - 1; jj >= s0; --jj) {
-                float w = 0.0f, dpw = 0.0f;
-                if (cbeg + (uint32_t)jj < last) {
-                    const float4 m = s_m[jj];
-                    const float4 c = s_c[jj];
-                    const float dx = pix_offset(pxc, m.x, m.z);
-                    const float dy = pix_offset(pyc, m.y, m.w);
-                    float g;
-                    const float a = surfel_alpha(dx, dy, c.x, c.y, c.z, c.w, amax, g);
-                    if (a >= amin) {
-                        const float oma = __fsub_rn(1.0f, a);
-                        T = __fdiv_rn(T, oma);   // T_k
-                        w = a * T;
-                        const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
-                        float D = 0.0f;
-#pragma unroll
-                        for (int q = 0; q < NCP / 4; ++q) {
-                            const float4 f = f4[q];
-                            D = fmaf(G[4 * q], f.x, D);
-                            D = fmaf(G[4 * q + 1], f.y, D);
-                            D = fmaf(G[4 * q + 2], f.z, D);
-                            D = fmaf(G[4 * q + 3], f.w, D);
-                        }
-                        const float da = fmaf(T, D, -Ssum / oma);
-                        Ssum = fmaf(w, D, Ssum);
-                        const float4 f0 = f4[0];
-                        cr0 = fmaf(w, f0.x, cr0);
-                        cr1 = fmaf(w, f0.y, cr1);
-                        cr2 = fmaf(w, f0.z, cr2);
-                        const float ag = c.w * g;
-                        if (ag < amax) dpw = da * ag;   // d alpha = dpw / alpha
-                    }
-                }
-                const int r = jj - s0;
-                s_w[r * SP + lane] = w;
-                s_p[r * SP + lane] = dpw;
-            }
-            __syncwarp();
-            // phase B (lane = entry): reduce the entry's gradient over the warp's 32 pixels
-            if (lane < sb - s0) {
-                const int e = s0 + lane;
-                const float4 m = s_m[e];
-                const float4 c = s_c[e];
-                float acc[NCP];
-#pragma unroll
-                for (int ch = 0; ch < NCP; ++ch) acc[ch] = 0.0f;
-                float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, g3 = 0.0f, g4 = 0.0f, g5 = 0.0f;
-                bool any = false;
-                const float* rw = s_w + lane * SP;
-                const float* rp = s_p + lane * SP;
-                for (int p = 0; p < 32; ++p) {
-                    const float w = rw[p];
-                    if (w != 0.0f) {
-                        any = true;
-#pragma unroll
-                        for (int ch = 0; ch < NCP; ++ch) acc[ch] = fmaf(w, s_G[ch * SP + p], acc[ch]);
-                        const float dpw = rp[p];
-                        const float dx = pix_offset((float)(wx0 + (p & 7)) + 0.5f, m.x, m.z);
-                        const float dy = pix_offset((float)(wy0 + (p >> 3)) + 0.5f, m.y, m.w);
-                        g0 = fmaf(dpw, c.x * dx + c.y * dy, g0);
-                        g1 = fmaf(dpw, c.y * dx + c.z * dy, g1);
-                        g2 = fmaf(-0.5f * dpw, dx * dx, g2);
-                        g3 = fmaf(-dpw, dx * dy, g3);
-                        g4 = fmaf(-0.5f * dpw, dy * dy, g4);
-                        g5 += dpw;
-                    }
-                }
-                if (any) {
-                    float* dst = s_g + e * GPS;
-                    atomicAdd(dst + 0, g0);
-                    atomicAdd(dst + 1, g1);
-                    atomicAdd(dst + 2, g2);
-                    atomicAdd(dst + 3, g3);
-                    atomicAdd(dst + 4, g4);
-                    atomicAdd(dst + 5, g5 / c.w);
-#pragma unroll
-                    for (int ch = 0; ch < NCP; ++ch)
-                        if (ch < nch && 6 + ch < GP) atomicAdd(dst + 6 + ch, acc[ch]);
-                }
-            }
-            __syncwarp();
+    for (uint32_t cend = wmax; cend > 0;) {
+        const uint32_t cbeg = cend > 32u ? cend - 32u : 0u;
+        const uint32_t j = cbeg + lane;   // index in the tile list
+        bool hit = false;
+        uint32_t rec = 0;
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
+        if (j < cend) {
+            rec = pair_rec[start + j];
+            const float4* r4 = reinterpret_cast<const float4*>(recs + rec);
+            m = r4[0];
+            c = r4[1];
+            hit = entry_hits_block(m, c, amin, (float)bx, (float)by);
         }
-        __syncthreads();
-        for (int q = threadIdx.x; q < cnt * GP; q += BLK) {
-            const int e = q / GP, ch = q - e * GP;
-            const float val = s_g[e * GPS + ch];
-            if (val != 0.0f) atomicAdd(&rec_grad[(unsigned long long)s_rec[e] * GP + ch], val);
-        }
-        __syncthreads();
+        const unsigned mask = __ballot_sync(kFull, hit);
         cend = cbeg;
+        if (!mask) continue;
+        const int h = __popc(mask);
+        if (hit) {
+            const int slot = __popc(mask & lt_mask);
+            s_m[slot] = m;
+            s_c[slot] = c;
+            s_rec[slot] = rec;
+            s_idx[slot] = j;
+            const float4 d = reinterpret_cast<const float4*>(recs + rec)[2];
+            stage_features_bwd<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
+        }
+        __syncwarp();
+        // phase A (lane = pixel): reverse recursion over the compacted entries
+        unsigned pmask = 0;
+        for (int jj = h - 1; jj >= 0; --jj) {
+            float w = 0.0f, dpw = 0.0f;
+            if (s_idx[jj] < last) {
+                const float4 mm = s_m[jj];
+                const float4 cc = s_c[jj];
+                const float dx = pix_offset(pxc, mm.x, mm.z);
+                const float dy = pix_offset(pyc, mm.y, mm.w);
+                float g;
+                const float a = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
+                if (a >= amin) {
+                    const float oma = __fsub_rn(1.0f, a);
+                    T = __fdiv_rn(T, oma);   // T_k
+                    w = a * T;
+                    const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
+                    float D = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < NCP / 4; ++q) {
+                        const float4 f = f4[q];
+                        D = fmaf(G[4 * q], f.x, D);
+                        D = fmaf(G[4 * q + 1], f.y, D);
+                        D = fmaf(G[4 * q + 2], f.z, D);
+                        D = fmaf(G[4 * q + 3], f.w, D);
+                    }
+                    const float da = fmaf(T, D, -Ssum / oma);
+                    Ssum = fmaf(w, D, Ssum);
+                    const float4 f0 = f4[0];
+                    cr0 = fmaf(w, f0.x, cr0);
+                    cr1 = fmaf(w, f0.y, cr1);
+                    cr2 = fmaf(w, f0.z, cr2);
+                    const float ag = cc.w * g;
+                    if (ag < amax) dpw = da * ag;   // d alpha = dpw / alpha
+                }
+            }
+            s_w[jj * SP + lane] = w;
+            s_p[jj * SP + lane] = dpw;
+            pmask |= __ballot_sync(kFull, w != 0.0f);
+        }
+        __syncwarp();
+        // phase B (lane = entry): sum the entry's gradient over the pixels that got anything
+        bool any = false;
+        if (lane < h) {
+            const int e = lane;
+            const float4 mm = s_m[e];
+            const float4 cc = s_c[e];
+            float acc[NCP];
+#pragma unroll
+            for (int ch = 0; ch < NCP; ++ch) acc[ch] = 0.0f;
+            float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, g3 = 0.0f, g4 = 0.0f, g5 = 0.0f;
+            for (unsigned q = pmask; q; q &= q - 1) {
+                const int p = __ffs(q) - 1;
+                const float w = s_w[e * SP + p];
+                if (w == 0.0f) continue;
+                any = true;
+#pragma unroll
+                for (int ch = 0; ch < NCP; ++ch) acc[ch] = fmaf(w, s_G[ch * SP + p], acc[ch]);
+                const float dpw = s_p[e * SP + p];
+                const float dx = pix_offset((float)(bx + (p & 7)) + 0.5f, mm.x, mm.z);
+                const float dy = pix_offset((float)(by + (p >> 3)) + 0.5f, mm.y, mm.w);
+                g0 = fmaf(dpw, cc.x * dx + cc.y * dy, g0);
+                g1 = fmaf(dpw, cc.y * dx + cc.z * dy, g1);
+                g2 = fmaf(-0.5f * dpw, dx * dx, g2);
+                g3 = fmaf(-dpw, dx * dy, g3);
+                g4 = fmaf(-0.5f * dpw, dy * dy, g4);
+                g5 += dpw;
+            }
+            if (any) {   // the entry's row of the tables becomes its gradient row
+                float* r0 = s_w + e * SP;
+                float* r1 = s_p + e * SP;
+                r0[0] = g0; r0[1] = g1; r0[2] = g2; r0[3] = g3; r0[4] = g4; r0[5] = g5 / cc.w;
+#pragma unroll
+                for (int ch = 0; ch < NCP; ++ch) {
+                    const int col = 6 + ch;
+                    if (col < SP) r0[col] = acc[ch];
+                    else r1[col - SP] = acc[ch];
+                }
+            }
+        }
+        const unsigned anym = __ballot_sync(kFull, any);
+        __syncwarp();
+        // one coalesced atomic per (entry, channel)
+        for (unsigned q = anym; q; q &= q - 1) {
+            const int e = __ffs(q) - 1;
+            float* dst = rec_grad + (unsigned long long)s_rec[e] * GP;
+            for (int col = lane; col < 6 + nch; col += 32) {
+                const float val = col < SP ? s_w[e * SP + col] : s_p[e * SP + col - SP];
+                if (val != 0.0f) atomicAdd(dst + col, val);
+            }
+        }
+        __syncwarp();
     }
 
     // exposure (Eq. 7): dL/db = sum g', dL/da = sum g' e^a c_raw
@@ -246,21 +246,15 @@ __global__ void __launch_bounds__(TW * TH) composite_bwd_k(const ViewParams* __r
         e_a += __shfl_xor_sync(kFull, e_a, o);
         e_b += __shfl_xor_sync(kFull, e_b, o);
     }
-    if (lane == 0) { s_exp[warp][0] = e_a; s_exp[warp][1] = e_b; }
-    __syncthreads();
-    if (threadIdx.x == 0 && d_exposure) {
-        float ta = 0.0f, tb = 0.0f;
-        for (int w = 0; w < NW; ++w) { ta += s_exp[w][0]; tb += s_exp[w][1]; }
-        if (ta != 0.0f) atomicAdd(&d_exposure[2 * v.exp_idx], ta);
-        if (tb != 0.0f) atomicAdd(&d_exposure[2 * v.exp_idx + 1], tb);
+    if (lane == 0 && d_exposure) {
+        if (e_a != 0.0f) atomicAdd(&d_exposure[2 * v.exp_idx], e_a);
+        if (e_b != 0.0f) atomicAdd(&d_exposure[2 * v.exp_idx + 1], e_b);
     }
 }
 
-static size_t bwd_smem_bytes(int blk, int ncp, int gp) {
-    const size_t ch = blk < kBwdChunk ? blk : kBwdChunk;
-    const size_t staged = ch * (32 + 4 * (size_t)ncp + 4 + 4 * (size_t)(gp + 1));
-    const size_t per_warp = 4 * (size_t)(ncp + 2 * 32) * kSubPad;
-    return staged + (size_t)(blk / 32) * per_warp;
+static size_t bwd_smem_bytes(int ncp) {
+    return (size_t)kBwdWarpsPerBlock * 4 *
+           (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 32 + 2 * 32 * kSubPad + ncp * kSubPad);
 }
 
 template <int TW, int TH>
@@ -268,19 +262,20 @@ static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
                             Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
                             const float* exposure_ab, const float* grad_out, const float* pix_T,
                             const uint32_t* pix_last, float* rec_grad, float* d_exposure) {
-    dim3 grid((unsigned)total_tiles);
+    constexpr int groups = TW * TH / 32 / kBwdWarpsPerBlock;
+    dim3 grid((unsigned)(total_tiles * groups));
 #define ROGS_BWD(NCP, GP)                                                                                        \
     do {                                                                                                         \
-        const size_t sm = bwd_smem_bytes(TW * TH, NCP, GP);                                                      \
+        const size_t sm = bwd_smem_bytes(NCP);                                                                   \
         static bool attr_set = false;                                                                            \
         if (!attr_set) {                                                                                         \
             cudaFuncSetAttribute(composite_bwd_k<TW, TH, NCP, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  (int)sm);                                                                       \
             attr_set = true;                                                                                     \
         }                                                                                                        \
-        composite_bwd_k<TW, TH, NCP, GP><<<grid, TW * TH, sm, s>>>(views, n_views, k, sp, recs, pair_rec,        \
-                                                                   ranges, exposure_ab, grad_out, pix_T,         \
-                                                                   pix_last, rec_grad, d_exposure);              \
+        composite_bwd_k<TW, TH, NCP, GP><<<grid, 32 * kBwdWarpsPerBlock, sm, s>>>(                               \
+            views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab, grad_out, pix_T, pix_last, rec_grad,     \
+            d_exposure);                                                                                         \
         note_launches(1);                                                                                        \
     } while (0)
     switch (ncp) {

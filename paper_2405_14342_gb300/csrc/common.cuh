@@ -155,6 +155,20 @@ __device__ __forceinline__ float surfel_alpha(float dx, float dy, float A, float
     return fminf(alpha_max, __fmul_rn(alpha, g));
 }
 
+// Conservative test: can the entry reach a >= alpha_min at some pixel centre
+// of the 8x4 block whose first pixel is (bx, by)?  Uses the bounding box of
+// the ellipse d^T Q d <= 2 ln(alpha / alpha_min) (Q = conic), padded so that
+// binary32 rounding never drops a pixel the exact per-pixel test would keep.
+__device__ __forceinline__ bool entry_hits_block(float4 m, float4 c, float alpha_min, float bx, float by) {
+    const float det = c.x * c.z - c.y * c.y;
+    if (!(det > 0.0f)) return true;   // degenerate: keep
+    const float kap = fmaxf(2.0f * logf(c.w / alpha_min), 0.0f);
+    const float rx = sqrtf(kap * c.z / det) * 1.002f + 0.01f;
+    const float ry = sqrtf(kap * c.x / det) * 1.002f + 0.01f;
+    const float mx = m.x + m.z, my = m.y + m.w;
+    return (mx + rx >= bx + 0.5f) && (mx - rx <= bx + 7.5f) && (my + ry >= by + 0.5f) && (my - ry <= by + 3.5f);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -5,14 +5,15 @@
 // semantic logits ("the color c is replaced by the semantic vector") and the
 // camera depth; Eq. 7 applies the per-camera exposure e^a c + b to rgb.
 //
-// One CTA per tile (tile_w x tile_h pixels, one pixel per thread; each warp
-// covers an 8x4 pixel block so its lanes see similar lists).  The tile's
-// list is processed in chunks of one entry per thread: each thread stages
-// one entry's record (two 16-byte loads) and its features (rgb, sem, depth)
-// into shared memory; then every thread walks the chunk from shared memory
-// (broadcast reads).  A pixel stops before the entry that would take its
-// transmittance below t_min; the CTA leaves the list once all its pixels
-// have stopped (__syncthreads_count).
+// One CTA per tile; each warp owns an 8x4 pixel block of the tile (one
+// pixel per lane) and walks the tile's depth-ordered list on its own, 32
+// entries at a time: the lanes read one record each, keep only the entries
+// whose footprint can reach the warp's block (a conservative ellipse
+// bounding box), compact them in order into the warp's shared-memory slots
+// together with their features (rgb, sem, depth), and then every lane walks
+// the compacted entries for its pixel.  A warp stops as soon as all its
+// pixels have stopped (transmittance stop), without waiting for the rest of
+// the tile: there is no block-wide barrier.
 #include "kernels.h"
 
 namespace rogs {
@@ -27,27 +28,22 @@ int padded_channels(int C) {
     return 64;
 }
 
+// Features of surfel s (rgb, C logits, depth) into a shared-memory row of NCP floats.
 template <int NCP>
-__device__ __forceinline__ void stage_entry(const Record* __restrict__ recs, const uint32_t rec, const SurfelPtrs& sp,
-                                            int C, float4* s_m, float4* s_c, float* s_f, int slot) {
-    const float4* r4 = reinterpret_cast<const float4*>(recs + rec);
-    const float4 a = r4[0];
-    const float4 b = r4[1];
-    const float4 c = r4[2];
-    s_m[slot] = a;
-    s_c[slot] = b;
-    const uint32_t s = __float_as_uint(c.z);
-    float* f = s_f + slot * NCP;
+__device__ __forceinline__ void stage_features(float* f, uint32_t s, float depth, const SurfelPtrs& sp, int C) {
     f[0] = sp.rgb[3ull * s];
     f[1] = sp.rgb[3ull * s + 1];
     f[2] = sp.rgb[3ull * s + 2];
     const float* sem = sp.sem + (unsigned long long)C * s;
     for (int ch = 0; ch < C; ++ch) f[3 + ch] = sem[ch];
-    f[3 + C] = c.x;  // camera depth
+    f[3 + C] = depth;
 #pragma unroll
     for (int ch = 0; ch < NCP; ++ch)
         if (ch > 3 + C) f[ch] = 0.0f;
 }
+
+template <int NCP>
+__host__ __device__ constexpr int fwd_warp_floats() { return 32 * 4 + 32 * 4 + 32 * NCP + 32; }
 
 template <int TW, int TH, int NCP>
 __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __restrict__ views, int n_views, Consts k,
@@ -58,13 +54,14 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                                                            float* __restrict__ out, float* __restrict__ pix_T,
                                                            uint32_t* __restrict__ pix_last,
                                                            StateHeader* __restrict__ hdr) {
-    constexpr int BLK = TW * TH;
     constexpr int WX = TW / 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     extern __shared__ float4 smem_fwd[];
-    float4* s_m = smem_fwd;
-    float4* s_c = s_m + BLK;
-    float* s_f = reinterpret_cast<float*>(s_c + BLK);
-    __shared__ unsigned long long s_cnt;
+    float* wbase = reinterpret_cast<float*>(smem_fwd) + warp * fwd_warp_floats<NCP>();
+    float4* s_m = reinterpret_cast<float4*>(wbase);
+    float4* s_c = s_m + 32;
+    float* s_f = reinterpret_cast<float*>(s_c + 32);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_f + 32 * NCP);
 
     const long long tile = blockIdx.x;
     const int vi = view_of_tile(views, n_views, tile);
@@ -72,17 +69,16 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
     const int W = v.W, H = v.H;
     const long long lt = tile - v.tile_base;
     const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = tx * TW + (warp % WX) * 8 + (lane & 7);
-    const int py = ty * TH + (warp / WX) * 4 + (lane >> 3);
+    const int bx = tx * TW + (warp % WX) * 8, by = ty * TH + (warp / WX) * 4;
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     const uint2 rg = ranges[tile];
     const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
     const int C = k.C;
     const float amin = k.alpha_min, amax = k.alpha_max, tmin = k.t_min;
+    const unsigned lt_mask = lanemask_lt();
 
-    if (threadIdx.x == 0) s_cnt = 0ull;
     float T = 1.0f;
     float acc[NCP];
 #pragma unroll
@@ -90,20 +86,39 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
     uint32_t last = 0, ncomp = 0;
     bool done = !inside;
 
-    for (uint32_t base = start; base < end; base += BLK) {
-        if (__syncthreads_count(done) == BLK) break;
-        const uint32_t j = base + threadIdx.x;
-        if (j < end) stage_entry<NCP>(recs, pair_rec[j], sp, C, s_m, s_c, s_f, threadIdx.x);
-        __syncthreads();
-        const int cnt = (int)min((uint32_t)BLK, end - base);
+    for (uint32_t base = start; base < end; base += 32) {
+        if (__all_sync(kFull, done)) break;
+        const uint32_t j = base + lane;
+        bool hit = false;
+        uint32_t rec = 0;
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
+        if (j < end) {
+            rec = pair_rec[j];
+            const float4* r4 = reinterpret_cast<const float4*>(recs + rec);
+            m = r4[0];
+            c = r4[1];
+            hit = entry_hits_block(m, c, amin, (float)bx, (float)by);
+        }
+        const unsigned mask = __ballot_sync(kFull, hit);
+        if (!mask) continue;
+        if (hit) {
+            const int slot = __popc(mask & lt_mask);
+            s_m[slot] = m;
+            s_c[slot] = c;
+            s_idx[slot] = j - start + 1;
+            const float4 d = reinterpret_cast<const float4*>(recs + rec)[2];
+            stage_features<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
+        }
+        __syncwarp();
+        const int h = __popc(mask);
         if (!done) {
-            for (int jj = 0; jj < cnt; ++jj) {
-                const float4 m = s_m[jj];
-                const float4 c = s_c[jj];
-                const float dx = pix_offset(pxc, m.x, m.z);
-                const float dy = pix_offset(pyc, m.y, m.w);
+            for (int jj = 0; jj < h; ++jj) {
+                const float4 mm = s_m[jj];
+                const float4 cc = s_c[jj];
+                const float dx = pix_offset(pxc, mm.x, mm.z);
+                const float dy = pix_offset(pyc, mm.y, mm.w);
                 float g;
-                const float a = surfel_alpha(dx, dy, c.x, c.y, c.z, c.w, amax, g);
+                const float a = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
                 if (a < amin) continue;
                 const float Tn = __fmul_rn(T, __fsub_rn(1.0f, a));
                 if (Tn < tmin) {
@@ -121,10 +136,11 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                     acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
                 }
                 T = Tn;
-                last = base + jj + 1 - start;
+                last = s_idx[jj];
                 ++ncomp;
             }
         }
+        __syncwarp();
     }
 
     if (inside) {
@@ -143,16 +159,13 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
         pix_last[pix] = last;
     }
     // composited-pair counter (E_alg)
-    unsigned long long c = ncomp;
+    unsigned long long cnt = ncomp;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-    __syncthreads();
-    if (lane == 0 && c) atomicAdd(&s_cnt, c);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_cnt) atomicAdd(&hdr->composited, s_cnt);
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    if (lane == 0 && cnt) atomicAdd(&hdr->composited, cnt);
 }
 
-static size_t fwd_smem_bytes(int blk, int ncp) { return (size_t)blk * (32 + 4 * (size_t)ncp); }
+static size_t fwd_smem_bytes(int blk, int ncp) { return (size_t)(blk / 32) * 4 * (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32); }
 
 template <int TW, int TH>
 static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
