@@ -118,9 +118,11 @@ typedef struct {
      tile_range  uint32[2] per tile: [start, end) into pair_rec
      pix_T       float per pixel: final transmittance
      pix_last    uint32 per pixel: entries of its tile list up to and including
-                 the last composited one */
+                 the last composited one
+     tile_order  uint32 per tile: tiles by descending list length (the order in
+                 which the compositing kernels are scheduled) */
 typedef struct {
-    uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, total_bytes;
+    uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, tile_order, total_bytes;
     int64_t total_tiles, total_pixels;
 } rogs_state_layout;
 

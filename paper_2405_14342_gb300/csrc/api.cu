@@ -227,6 +227,7 @@ rogs_state_layout layout_for(const rogs_config& cfg, long long total_tiles, long
     L.tile_range = off; off = align256(off + 8 * (size_t)total_tiles);
     L.pix_T = off; off = align256(off + 4 * (size_t)total_pix);
     L.pix_last = off; off = align256(off + 4 * (size_t)total_pix);
+    L.tile_order = off; off = align256(off + 4 * (size_t)total_tiles);
     L.total_bytes = off;
     L.total_tiles = total_tiles;
     L.total_pixels = total_pix;
@@ -472,6 +473,7 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     uint2* ranges = (uint2*)(sb + L.tile_range);
     float* pix_T = (float*)(sb + L.pix_T);
     uint32_t* pix_last = (uint32_t*)(sb + L.pix_last);
+    uint32_t* tile_order = (uint32_t*)(sb + L.tile_order);
     const unsigned long long rcap = (unsigned long long)cfg.record_capacity;
     const unsigned long long pcap = (unsigned long long)cfg.pair_capacity;
     const Consts k = make_consts(cfg);
@@ -498,9 +500,12 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     }
     ROGS_CUDA(ctx, cudaMemsetAsync(ranges, 0, 8 * (size_t)total_tiles, s));
     if (n > 0) tile_ranges(ctx->pk_b, hdr, pcap, ranges, s);
+    // longest lists first: the compositing kernels take their tiles in this order
+    order_tiles(ranges, total_tiles, tile_order, (unsigned long long)total_tiles <= pcap, ctx->pk_a, ctx->pv_a,
+                ctx->pk_c, ctx->pv_c, ctx->pk_b, ctx->hist, s);
     prof_mark(ctx, 4, s);
     composite_fwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
-                  exposure_ab, out, pix_T, pix_last, hdr, s);
+                  tile_order, exposure_ab, out, pix_T, pix_last, hdr, s);
     prof_mark(ctx, -1, s);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
@@ -557,13 +562,14 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     const uint2* ranges = (const uint2*)(sb + L.tile_range);
     const float* pix_T = (const float*)(sb + L.pix_T);
     const uint32_t* pix_last = (const uint32_t*)(sb + L.pix_last);
+    const uint32_t* tile_order = (const uint32_t*)(sb + L.tile_order);
     const Consts k = make_consts(cfg);
     const SurfelPtrs sp{surfels->xyz, surfels->scale, surfels->quat, surfels->opacity, surfels->rgb, surfels->sem,
                         surfels->n};
     const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
     prof_mark(ctx, 6, s);
     composite_bwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
-                  exposure_ab, grad_out, pix_T, pix_last, ctx->rec_grad, grads->exposure, s);
+                  tile_order, exposure_ab, grad_out, pix_T, pix_last, ctx->rec_grad, grads->exposure, s);
     prof_mark(ctx, 7, s);
     project_bwd(views, k, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp,
                 s);

@@ -51,7 +51,8 @@ __host__ __device__ constexpr int bwd_warp_floats() {
 template <int TW, int TH, int NCP, int GP>
 __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
     const ViewParams* __restrict__ views, int n_views, Consts k, SurfelPtrs sp, const Record* __restrict__ recs,
-    const uint32_t* __restrict__ pair_rec, const uint2* __restrict__ ranges, const float* __restrict__ exposure_ab,
+    const uint32_t* __restrict__ pair_rec, const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order,
+    const float* __restrict__ exposure_ab,
     const float* __restrict__ grad_out, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
     float* __restrict__ rec_grad, float* __restrict__ d_exposure) {
     constexpr int WX = TW / 8;
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
     constexpr int SP = kSubPad;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const long long tile = blockIdx.x / GROUPS;
+    const long long tile = tile_order[blockIdx.x / GROUPS];
     const int warp = (int)(blockIdx.x % GROUPS) * kBwdWarpsPerBlock + wib;   // warp index inside the tile
     extern __shared__ float4 smem_bwd[];
     float* wbase = reinterpret_cast<float*>(smem_bwd) + wib * bwd_warp_floats<NCP>();
@@ -260,7 +261,7 @@ static size_t bwd_smem_bytes(int ncp) {
 template <int TW, int TH>
 static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
                             Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                            const float* exposure_ab, const float* grad_out, const float* pix_T,
+                            const uint32_t* tile_order, const float* exposure_ab, const float* grad_out, const float* pix_T,
                             const uint32_t* pix_last, float* rec_grad, float* d_exposure) {
     constexpr int groups = TW * TH / 32 / kBwdWarpsPerBlock;
     dim3 grid((unsigned)(total_tiles * groups));
@@ -274,7 +275,8 @@ static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
             attr_set = true;                                                                                     \
         }                                                                                                        \
         composite_bwd_k<TW, TH, NCP, GP><<<grid, 32 * kBwdWarpsPerBlock, sm, s>>>(                               \
-            views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab, grad_out, pix_T, pix_last, rec_grad,     \
+            views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, grad_out, pix_T, pix_last,   \
+            rec_grad,                                                                                            \
             d_exposure);                                                                                         \
         note_launches(1);                                                                                        \
     } while (0)
@@ -291,17 +293,17 @@ static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
 
 void composite_bwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
                    Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                   const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,
+                   const uint32_t* tile_order, const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,
                    float* rec_grad, float* d_exposure, cudaStream_t s) {
     const int ncp = padded_channels(C);
     if (tile_w == 32 && tile_h == 8)
-        launch_bwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab,
+        launch_bwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab,
                                grad_out, pix_T, pix_last, rec_grad, d_exposure);
     else if (tile_w == 8 && tile_h == 8)
-        launch_bwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab,
+        launch_bwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab,
                               grad_out, pix_T, pix_last, rec_grad, d_exposure);
     else
-        launch_bwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab,
+        launch_bwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab,
                                 grad_out, pix_T, pix_last, rec_grad, d_exposure);
 }
 

@@ -100,4 +100,30 @@ void tile_ranges(const uint32_t* sorted_tile, const StateHeader* hdr, unsigned l
     note_launches(1);
 }
 
+__global__ void __launch_bounds__(256) tile_keys_k(const uint2* __restrict__ ranges, long long n_tiles,
+                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                   uint32_t* __restrict__ order, int sort_ok) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_tiles;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (!sort_ok) {
+            order[t] = (uint32_t)t;
+            continue;
+        }
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+        keys[t] = 0xffffu - (len < 0xffffu ? len : 0xffffu);   // ascending key = descending length
+        vals[t] = (uint32_t)t;
+    }
+}
+
+void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool sort_ok, uint32_t* ka, uint32_t* va,
+                 uint32_t* kb, uint32_t* vb, uint32_t* kalt, uint32_t* hist, cudaStream_t s) {
+    long long blocks = (n_tiles + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    tile_keys_k<<<(int)blocks, 256, 0, s>>>(ranges, n_tiles, ka, va, order, sort_ok ? 1 : 0);
+    note_launches(1);
+    if (sort_ok) radix_sort_pairs(ka, va, kb, order, kalt, vb, nullptr, (unsigned long long)n_tiles, 16, hist, s);
+}
+
 }  // namespace rogs

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                                                            SurfelPtrs sp, const Record* __restrict__ recs,
                                                            const uint32_t* __restrict__ pair_rec,
                                                            const uint2* __restrict__ ranges,
+                                                           const uint32_t* __restrict__ tile_order,
                                                            const float* __restrict__ exposure_ab,
                                                            float* __restrict__ out, float* __restrict__ pix_T,
                                                            uint32_t* __restrict__ pix_last,
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
     float* s_f = reinterpret_cast<float*>(s_c + 32);
     uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_f + 32 * NCP);
 
-    const long long tile = blockIdx.x;
+    const long long tile = tile_order[blockIdx.x];
     const int vi = view_of_tile(views, n_views, tile);
     const ViewParams& v = views[vi];
     const int W = v.W, H = v.H;
@@ -170,7 +171,8 @@ static size_t fwd_smem_bytes(int blk, int ncp) { return (size_t)(blk / 32) * 4 *
 template <int TW, int TH>
 static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
                             Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                            const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr) {
+                            const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T,
+                            uint32_t* pix_last, StateHeader* hdr) {
     dim3 grid((unsigned)total_tiles);
 #define ROGS_FWD(NCP)                                                                                          \
     do {                                                                                                       \
@@ -182,7 +184,8 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
             attr_set = true;                                                                                   \
         }                                                                                                      \
         composite_fwd_k<TW, TH, NCP><<<grid, TW * TH, sm, s>>>(views, n_views, k, sp, recs, pair_rec, ranges, \
-                                                               exposure_ab, out, pix_T, pix_last, hdr);       \
+                                                               tile_order, exposure_ab, out, pix_T, pix_last, \
+                                                               hdr);                                          \
         note_launches(1);                                                                                      \
     } while (0)
     switch (ncp) {
@@ -198,17 +201,17 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
 
 void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
                    Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                   const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
+                   const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
                    cudaStream_t s) {
     const int ncp = padded_channels(C);
     if (tile_w == 32 && tile_h == 8)
-        launch_fwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab, out,
+        launch_fwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, out,
                                pix_T, pix_last, hdr);
     else if (tile_w == 8 && tile_h == 8)
-        launch_fwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab, out,
+        launch_fwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, out,
                               pix_T, pix_last, hdr);
     else
-        launch_fwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, exposure_ab, out,
+        launch_fwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, out,
                                 pix_T, pix_last, hdr);
 }
 

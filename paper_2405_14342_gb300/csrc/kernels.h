@@ -54,19 +54,23 @@ void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Recor
 void tile_ranges(const uint32_t* sorted_tile, const StateHeader* hdr, unsigned long long pair_cap, uint2* ranges,
                  cudaStream_t s);
 void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s);
+// Tile order by descending list length (identity when sort_ok is false);
+// uses ka/va/kb/vb/kalt (>= n_tiles uint32 each) and the radix histogram.
+void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool sort_ok, uint32_t* ka, uint32_t* va,
+                 uint32_t* kb, uint32_t* vb, uint32_t* kalt, uint32_t* hist, cudaStream_t s);
 
 // ---- composite.cu
 int padded_channels(int C);
 void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
                    Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                   const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
+                   const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
                    cudaStream_t s);
 
 // ---- backward.cu
 int grad_channels(int C);  // per-record gradient stride (32 or 64)
 void composite_bwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
                    Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                   const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,
+                   const uint32_t* tile_order, const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,
                    float* rec_grad, float* d_exposure, cudaStream_t s);
 void project_bwd(const ViewParams* views, Consts k, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
                  unsigned long long rec_cap, float* rec_grad, int C, GradPtrs g, cudaStream_t s);
