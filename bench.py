@@ -141,6 +141,26 @@ def make_targets(R, renderer, m_pert, rigs, exposure):
 
 # --------------------------------------------------------------- our arm
 
+def _timed(fn, steps, world, dist):
+    """Run fn(k) for k in range(steps) between CUDA events; max over ranks (ms)."""
+    import torch
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        fn(k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -156,6 +176,8 @@ def run_ours(args):
     tile = tuple(int(x) for x in args.tile.split("x"))
     n_t = args.timesteps
     m, field, rigs = build_workload(rank, C, world, n_t)
+    stream = torch.cuda.Stream()          # graphs need a non-default stream
+    torch.cuda.set_stream(stream)
     exposure = torch.as_tensor(scenes.exposure_params(6), device="cuda")
     rr = R.Renderer(C, record_capacity=args.record_capacity, pair_capacity=args.pair_capacity, tile=tile)
     rr.reserve(m.n, 6)
@@ -181,36 +203,31 @@ def run_ours(args):
     torch.cuda.synchronize()
     for fr in frames:
         rr.counts(fr)
-    # warm-up
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
 
+    # ---- batched, graph-captured form (headline): one graph per timestep
+    graphs = [rr.train_graph(st, frames[k], exposure, *targets[k], loss, gout, grads) for k in range(n_t)]
+    for k in range(args.warmup):
+        graphs[k % n_t].launch()
+    torch.cuda.synchronize()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     sampler = ClockSampler(vis.split(",")[local] if vis else local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
+    launches0 = rogs.rogs_launch_count()
+    ms = _timed(lambda k: graphs[(args.warmup + k) % n_t].launch(), args.steps, world, dist)
+    graph_nodes_per_step = None
+    clocks = sampler.stop()
+
+    # ---- batched eager form, with the per-stage profiler (the roofline's kernel times)
     rogs.rogs_profile_enable(rr.ctx, True)
     launches0 = rogs.rogs_launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for k in range(args.steps):
-        step(args.warmup + k)
-    e1.record()
-    torch.cuda.synchronize()
+    ms_eager = _timed(lambda k: step(args.warmup + k), args.steps, world, dist)
     launches = rogs.rogs_launch_count() - launches0
     prof = rogs.rogs_profile_read(rr.ctx)
     rogs.rogs_profile_enable(rr.ctx, False)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
 
     # per-step counts of the timed steps (deterministic per timestep)
     comp, nrec, npair = 0, 0, 0
@@ -220,45 +237,68 @@ def run_ours(args):
         nrec += c.n_records
         npair += c.n_pairs
 
-    # ---- end to end through the C-ABI with host buffers
+    # ---- plain form: one view per call (the per-view baseline)
+    ms_plain = None
+    if not args.no_plain:
+        n_tp = min(n_t, 8)
+        rp = R.Renderer(C, record_capacity=max(args.record_capacity // 4, 400_000),
+                        pair_capacity=max(args.pair_capacity // 4, 3_000_000), tile=tile)
+        rp.reserve(st.n, 1)
+        pframes, ptargets = [], []
+        for k in range(n_tp):
+            trgb, lab, msk = targets[k]
+            o3 = o1 = 0
+            for v, cam in enumerate(rigs[k]):
+                npx = cam.width * cam.height
+                pframes.append(rp.frame([cam]))
+                ptargets.append((trgb[o3: o3 + 3 * npx], lab[o1: o1 + npx], msk[o1: o1 + npx]))
+                o3 += 3 * npx
+                o1 += npx
+        pgout = torch.empty_like(pframes[0].out)
+
+        def step_plain(k):
+            base = (k % n_tp) * 6
+            for v in range(6):
+                fr = pframes[base + v]
+                a, b, c = ptargets[base + v]
+                rp.forward(st, fr, exposure)
+                rp.loss(fr, a, b, c, 1.0, 0.06, loss=loss, grad_out=pgout[: fr.out.numel()])
+                rp.backward(st, fr, exposure, pgout[: fr.out.numel()], grads=grads)
+
+        for k in range(n_tp):
+            for v in range(6):
+                rp.forward(st, pframes[k * 6 + v], exposure)
+        torch.cuda.synchronize()
+        for fr in pframes:
+            rp.counts(fr)
+        for k in range(args.warmup):
+            step_plain(k)
+        ms_plain = _timed(lambda k: step_plain(args.warmup + k), args.steps, world, dist)
+        del pframes, ptargets, rp
+
+    # ---- end to end through the C-ABI with host buffers (graph form)
     e2e = None
     if not args.no_e2e:
-        pinned = []
-        for k in range(min(8, n_t)):
-            a, b, c = targets[k]
-            pinned.append((a.cpu().pin_memory(), b.cpu().pin_memory(), c.cpu().pin_memory()))
-        dev = [torch.empty_like(x) for x in targets[0]]
+        n_h = min(8, n_t)
+        pinned = [tuple(x.cpu().pin_memory() for x in targets[k]) for k in range(n_h)]
         host_loss = torch.empty(1, pin_memory=True)
         h2d = sum(int(x.numel() * x.element_size()) for x in pinned[0])
 
         def step_host(k):
-            fr = frames[k % len(pinned)]
-            for d, h in zip(dev, pinned[k % len(pinned)]):
+            j = k % n_h
+            for d, h in zip(targets[j], pinned[j]):
                 d.copy_(h, non_blocking=True)
-            rr.forward(st, fr, exposure)
-            rr.loss(fr, dev[0], dev[1], dev[2], 1.0, 0.06, loss=loss, grad_out=gout)
-            rr.backward(st, fr, exposure, gout, grads=grads)
+            graphs[j].launch()
             host_loss.copy_(loss, non_blocking=True)
 
-        for k in range(max(args.warmup, 1)):
+        for k in range(args.warmup):
             step_host(k)
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record()
-        for k in range(args.steps):
-            step_host(k)
-        a1.record()
-        torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = _timed(lambda k: step_host(args.warmup + k), args.steps, world, dist)
         e2e = {"value": round(world * args.steps * P / (ems * 1e-3) / 1e6, 3), "unit": "Mpix/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
 
+    for g in graphs:
+        g.close()
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -270,7 +310,6 @@ def run_ours(args):
     E = comp / args.steps
     nr = nrec / args.steps
     K = npair / args.steps
-    # algorithmic work per launch of each stage
     feat = 4 * (3 + C)
     stage_work = {
         "composite_fwd": (P * (4 * nch + 8) + 4 * K + nr * (48 + feat), E * (2 * nch + 18)),
@@ -293,7 +332,10 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": round(b / t / 1e9, 1), "peak": hbm, "unit": "GB/s"}
     roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
     roof["kernel"] = dom
-    roof["peak_source"] = peak_kind if roof["bound"] == "hbm" else "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"
+    roof["peak_source"] = (peak_kind + " (MEASURED_PEAKS hbm_gbs)") if roof["bound"] == "hbm" else \
+        "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"
+    roof["duration_ms"] = round(stage_ms[dom], 4)
+    roof["work_per_launch"] = {"bytes": round(b), "flops": round(f)}
     src = os.path.join(ROOT, "paper_2405_14342_gb300", "csrc",
                        "backward.cu" if dom in ("composite_bwd", "project_bwd") else "composite.cu")
     tr = NCU_TRAFFIC.get(dom)
@@ -306,10 +348,19 @@ def run_ours(args):
         "config": {"workload": "scene: 400x40 m strip, 0.1 m grid (1.6M surfels), C=19, 6x 960x540 surround "
                                "pinhole cams at 1.5 m, one fwd+loss+bwd per timestep (t=8..39)",
                    "surfels": st.n, "views_per_step": 6, "pixels_per_step": P, "classes": C,
-                   "tile": args.tile, "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "tile": args.tile, "form": "batched (6 views per launch), CUDA-graph replay per timestep",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
                    "timesteps_resident": n_t,
                    "l2": f"inputs larger than L2: 205 MB map + {n_t} timesteps of targets/outputs resident, "
                          "steps rotate"},
+        "forms": {
+            "batched_graph": {"value": round(value, 3), "ms_per_step": round(ms / args.steps, 4)},
+            "batched_eager": {"value": round(world * args.steps * P / (ms_eager * 1e-3) / 1e6, 3),
+                              "ms_per_step": round(ms_eager / args.steps, 4)},
+            "plain_per_view": None if ms_plain is None else {
+                "value": round(world * args.steps * P / (ms_plain * 1e-3) / 1e6, 3),
+                "ms_per_step": round(ms_plain / args.steps, 4)},
+        },
         "roofline": roof,
         "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof.items()},
         "counts_per_step": {"records": round(nr), "pairs": round(K), "composited": round(E)},
@@ -346,17 +397,23 @@ def numpy_targets(cams, C, seed=3):
 
 
 def cpu_baseline(args, rigs=None, budget_s=20.0):
+    """The oracle as it stands on this host's cores, on a bounded pixel sample
+    of the bench workload (time = fixed projection cost + per-pixel cost; the
+    sample size is chosen from two calibration runs to fill `budget_s`)."""
     import oracle
     from paper_2405_14342_gb300 import scenes
     m, field = scenes.strip_map(C=19, seed=0)
     cams = rigs[0] if rigs else scenes.surround_rig(field, T_FIRST)
     ex = scenes.exposure_params(6)
     tg = numpy_targets(cams, 19)
-    t0 = time.time()
-    npx, _ = oracle_step(m, cams, ex, tg, 64, seed=0)       # calibration
-    dt = time.time() - t0
-    per = max(64, int(64 * budget_s / max(dt, 1e-3) * 0.8))
-    per = min(per, 20000)
+    ts = []
+    for n in (32, 128):
+        t0 = time.time()
+        oracle_step(m, cams, ex, tg, n, seed=0)
+        ts.append(time.time() - t0)
+    per_px = max((ts[1] - ts[0]) / 96.0, 1e-6)
+    fixed = max(ts[0] - 32 * per_px, 0.0)
+    per = int(max(64, min(50000, (budget_s - fixed) / per_px)))
     t0 = time.time()
     npx, _ = oracle_step(m, cams, ex, tg, per, seed=1)
     dt = time.time() - t0
@@ -405,6 +462,7 @@ def main():
     ap.add_argument("--pair-capacity", type=int, default=12_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-pixels", type=int, default=200)
     ap.add_argument("--timesteps", type=int, default=T_COUNT, help="timesteps kept resident (profiling: fewer)")

@@ -221,6 +221,37 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
 rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
                             int32_t key_bits, uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream);
 
+/* ------------------------------------------------------ graph capture */
+
+typedef struct rogs_graph rogs_graph;
+
+/* Capture one training step -- rogs_render_fwd, rogs_loss and rogs_render_bwd
+   with exactly these arguments -- into a CUDA graph (the batched,
+   graph-captured form of the hot path: every view of the call is in each
+   stage's single launch, and replaying the graph removes the per-kernel
+   launch overhead).  All pointers are fixed in the graph; replays read the
+   current contents of the inputs and ADD into `grads` like rogs_render_bwd.
+   Scratch is sized before the capture starts (never during it).  `stream`
+   must not be the legacy default stream (NULL).  Argument errors are those of
+   the three calls.  On success *graph receives an executable graph owned by
+   the caller (free it with rogs_graph_destroy); ctx must outlive it. */
+rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
+                                    int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
+                                    void* state, const float* tgt_rgb, const int32_t* label, const uint8_t* mask,
+                                    float lambda_c, float lambda_s, float* loss, float* grad_out,
+                                    const rogs_grads* grads, rogs_stream stream, rogs_graph** graph);
+
+/* Same, forward only (rogs_render_fwd). */
+rogs_status rogs_render_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
+                                     int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
+                                     void* state, rogs_stream stream, rogs_graph** graph);
+
+/* Replay a captured graph on `stream` (asynchronous). */
+rogs_status rogs_graph_launch(rogs_graph* graph, rogs_stream stream);
+
+/* Free a captured graph. */
+void rogs_graph_destroy(rogs_graph* graph);
+
 /* Largest n accepted by rogs_sort_pairs_noalloc. */
 #define ROGS_NOALLOC_MAX_PAIRS 1048576
 

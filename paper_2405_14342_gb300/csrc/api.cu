@@ -23,6 +23,11 @@ static std::atomic<unsigned long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 }  // namespace rogs
 
+struct rogs_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct ProfEvent {
     int stage;
     cudaEvent_t a, b;
@@ -329,6 +334,8 @@ rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
         rogs_destroy(ctx);
         return st;
     }
+    prepare_composite_fwd();
+    prepare_composite_bwd();
     cudaDeviceSynchronize();
     *out = ctx;
     return ROGS_OK;
@@ -590,6 +597,86 @@ rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32
                      key_bits, ctx->hist, s);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
+}
+
+static rogs_status finish_capture(rogs_ctx* ctx, cudaStream_t s, rogs_status st, rogs_graph** out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != ROGS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess || !g) return fail(ctx, ROGS_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(ctx, ROGS_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    rogs_graph* gr = new rogs_graph();
+    gr->graph = g;
+    gr->exec = exec;
+    *out = gr;
+    return ROGS_OK;
+}
+
+static rogs_status begin_capture(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                                 cudaStream_t s, bool with_loss) {
+    if (!s) return fail(ctx, ROGS_ERR_INVALID, "graph capture needs a non-default stream");
+    if (!surfels || !cams || n_views < 1 || n_views > kMaxViews) return fail(ctx, ROGS_ERR_INVALID, "bad arguments");
+    static thread_local ViewsArg va;
+    long long tt, tp;
+    std::string err;
+    if (!make_views(ctx->cfg, cams, n_views, va, tt, tp, err)) return fail(ctx, ROGS_ERR_INVALID, err);
+    rogs_status st = ensure_bits(ctx, surfels->n, n_views, s);   // size scratch before capturing
+    if (st == ROGS_OK && with_loss) st = ensure_loss(ctx, tp, s);
+    if (st != ROGS_OK) return st;
+    ROGS_CUDA(ctx, cudaStreamSynchronize(s));
+    ROGS_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    return ROGS_OK;
+}
+
+rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
+                                    int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
+                                    void* state, const float* tgt_rgb, const int32_t* label, const uint8_t* mask,
+                                    float lambda_c, float lambda_s, float* loss, float* grad_out,
+                                    const rogs_grads* grads, rogs_stream stream, rogs_graph** gout) {
+    if (!ctx || !gout) return ROGS_ERR_INVALID;
+    *gout = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    rogs_status st = begin_capture(ctx, surfels, cams, n_views, s, true);
+    if (st != ROGS_OK) return st;
+    st = rogs_render_fwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, stream);
+    if (st == ROGS_OK)
+        st = rogs_loss(ctx, cams, n_views, out, tgt_rgb, label, mask, lambda_c, lambda_s, loss, grad_out, stream);
+    if (st == ROGS_OK)
+        st = rogs_render_bwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, state, grad_out, grads, stream);
+    return finish_capture(ctx, s, st, gout);
+}
+
+rogs_status rogs_render_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
+                                     int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
+                                     void* state, rogs_stream stream, rogs_graph** gout) {
+    if (!ctx || !gout) return ROGS_ERR_INVALID;
+    *gout = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    rogs_status st = begin_capture(ctx, surfels, cams, n_views, s, false);
+    if (st != ROGS_OK) return st;
+    st = rogs_render_fwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, stream);
+    return finish_capture(ctx, s, st, gout);
+}
+
+rogs_status rogs_graph_launch(rogs_graph* graph, rogs_stream stream) {
+    if (!graph || !graph->exec) return ROGS_ERR_INVALID;
+    if (cudaGraphLaunch(graph->exec, (cudaStream_t)stream) != cudaSuccess) return ROGS_ERR_CUDA;
+    return ROGS_OK;
+}
+
+void rogs_graph_destroy(rogs_graph* graph) {
+    if (!graph) return;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    delete graph;
 }
 
 rogs_status rogs_profile_enable(rogs_ctx* ctx, int32_t enable) {

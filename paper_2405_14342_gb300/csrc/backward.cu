@@ -258,27 +258,44 @@ static size_t bwd_smem_bytes(int ncp) {
            (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 32 + 2 * 32 * kSubPad + ncp * kSubPad);
 }
 
+template <int TW, int TH, int NCP, int GP>
+static void bwd_attr() {
+    static unsigned long long done_mask = 0;   // one bit per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !((done_mask >> dev) & 1ull)) {
+        cudaFuncSetAttribute(composite_bwd_k<TW, TH, NCP, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bwd_smem_bytes(NCP));
+        done_mask |= 1ull << dev;
+    }
+}
+
+template <int TW, int TH>
+static void prepare_bwd_tile() {
+    bwd_attr<TW, TH, 8, 32>(); bwd_attr<TW, TH, 12, 32>(); bwd_attr<TW, TH, 16, 32>();
+    bwd_attr<TW, TH, 24, 32>(); bwd_attr<TW, TH, 32, 64>(); bwd_attr<TW, TH, 64, 64>();
+}
+
+void prepare_composite_bwd() {
+    prepare_bwd_tile<16, 16>();
+    prepare_bwd_tile<32, 8>();
+    prepare_bwd_tile<8, 8>();
+}
+
 template <int TW, int TH>
 static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
                             Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                            const uint32_t* tile_order, const float* exposure_ab, const float* grad_out, const float* pix_T,
-                            const uint32_t* pix_last, float* rec_grad, float* d_exposure) {
+                            const uint32_t* tile_order, const float* exposure_ab, const float* grad_out,
+                            const float* pix_T, const uint32_t* pix_last, float* rec_grad, float* d_exposure) {
     constexpr int groups = TW * TH / 32 / kBwdWarpsPerBlock;
     dim3 grid((unsigned)(total_tiles * groups));
-#define ROGS_BWD(NCP, GP)                                                                                        \
-    do {                                                                                                         \
-        const size_t sm = bwd_smem_bytes(NCP);                                                                   \
-        static bool attr_set = false;                                                                            \
-        if (!attr_set) {                                                                                         \
-            cudaFuncSetAttribute(composite_bwd_k<TW, TH, NCP, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)sm);                                                                       \
-            attr_set = true;                                                                                     \
-        }                                                                                                        \
-        composite_bwd_k<TW, TH, NCP, GP><<<grid, 32 * kBwdWarpsPerBlock, sm, s>>>(                               \
-            views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, grad_out, pix_T, pix_last,   \
-            rec_grad,                                                                                            \
-            d_exposure);                                                                                         \
-        note_launches(1);                                                                                        \
+#define ROGS_BWD(NCP, GP)                                                                                      \
+    do {                                                                                                       \
+        bwd_attr<TW, TH, NCP, GP>();                                                                           \
+        composite_bwd_k<TW, TH, NCP, GP><<<grid, 32 * kBwdWarpsPerBlock, bwd_smem_bytes(NCP), s>>>(            \
+            views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, grad_out, pix_T, pix_last, \
+            rec_grad, d_exposure);                                                                             \
+        note_launches(1);                                                                                      \
     } while (0)
     switch (ncp) {
         case 8: ROGS_BWD(8, 32); break;

@@ -168,6 +168,30 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
 
 static size_t fwd_smem_bytes(int blk, int ncp) { return (size_t)(blk / 32) * 4 * (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32); }
 
+template <int TW, int TH, int NCP>
+static void fwd_attr() {
+    static unsigned long long done_mask = 0;   // one bit per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !((done_mask >> dev) & 1ull)) {
+        cudaFuncSetAttribute(composite_fwd_k<TW, TH, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fwd_smem_bytes(TW * TH, NCP));
+        done_mask |= 1ull << dev;
+    }
+}
+
+template <int TW, int TH>
+static void prepare_fwd_tile() {
+    fwd_attr<TW, TH, 8>(); fwd_attr<TW, TH, 12>(); fwd_attr<TW, TH, 16>();
+    fwd_attr<TW, TH, 24>(); fwd_attr<TW, TH, 32>(); fwd_attr<TW, TH, 64>();
+}
+
+void prepare_composite_fwd() {
+    prepare_fwd_tile<16, 16>();
+    prepare_fwd_tile<32, 8>();
+    prepare_fwd_tile<8, 8>();
+}
+
 template <int TW, int TH>
 static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
                             Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
@@ -176,16 +200,9 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
     dim3 grid((unsigned)total_tiles);
 #define ROGS_FWD(NCP)                                                                                          \
     do {                                                                                                       \
-        const size_t sm = fwd_smem_bytes(TW * TH, NCP);                                                        \
-        static bool attr_set = false;                                                                          \
-        if (!attr_set) {                                                                                       \
-            cudaFuncSetAttribute(composite_fwd_k<TW, TH, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                 (int)sm);                                                                     \
-            attr_set = true;                                                                                   \
-        }                                                                                                      \
-        composite_fwd_k<TW, TH, NCP><<<grid, TW * TH, sm, s>>>(views, n_views, k, sp, recs, pair_rec, ranges, \
-                                                               tile_order, exposure_ab, out, pix_T, pix_last, \
-                                                               hdr);                                          \
+        fwd_attr<TW, TH, NCP>();                                                                               \
+        composite_fwd_k<TW, TH, NCP><<<grid, TW * TH, fwd_smem_bytes(TW * TH, NCP), s>>>(                     \
+            views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, out, pix_T, pix_last, hdr); \
         note_launches(1);                                                                                      \
     } while (0)
     switch (ncp) {

@@ -61,6 +61,7 @@ void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool s
 
 // ---- composite.cu
 int padded_channels(int C);
+void prepare_composite_fwd();   // set the dynamic shared-memory limits (before any capture)
 void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
                    Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
                    const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
@@ -68,6 +69,7 @@ void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n
 
 // ---- backward.cu
 int grad_channels(int C);  // per-record gradient stride (32 or 64)
+void prepare_composite_bwd();
 void composite_bwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
                    Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
                    const uint32_t* tile_order, const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,

@@ -137,13 +137,31 @@ class Renderer:
                  grads: Optional[dict] = None, stream=None) -> dict:
         if grads is None:
             grads = zero_grads(m, exposure)
+        R.rogs_render_bwd(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.state,
+                          grad_out.contiguous(), self.grads_struct(grads), stream)
+        return grads
+
+    def grads_struct(self, grads: dict) -> R.rogs_grads:
         g = R.rogs_grads()
         for k in ("xyz", "scale", "quat", "opacity", "rgb", "sem", "exposure"):
             t = grads.get(k)
             setattr(g, k, t.data_ptr() if t is not None and t.numel() else None)
-        R.rogs_render_bwd(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.state,
-                          grad_out.contiguous(), g, stream)
-        return grads
+        return g
+
+    def train_graph(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, tgt_rgb, label, mask,
+                    loss: torch.Tensor, grad_out: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06,
+                    stream=None) -> "Graph":
+        """Capture forward + loss + backward of `frame` into a CUDA graph (all
+        pointers fixed; `stream` must be a non-default stream)."""
+        g = R.rogs_train_graph_create(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
+                                      frame.state, tgt_rgb, label, mask, lambda_c, lambda_s, loss, grad_out,
+                                      self.grads_struct(grads), stream)
+        return Graph(g, keep=(m, frame, exposure, tgt_rgb, label, mask, loss, grad_out, grads))
+
+    def render_graph(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, stream=None) -> "Graph":
+        g = R.rogs_render_graph_create(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
+                                       frame.state, stream)
+        return Graph(g, keep=(m, frame, exposure))
 
     def init_from_poses(self, grid_xy: torch.Tensor, poses: np.ndarray, exact_plane=True, stream=None):
         n = grid_xy.shape[0]
@@ -158,6 +176,28 @@ class Renderer:
         vo = torch.empty_like(vals)
         R.rogs_sort_pairs(self.ctx, keys, vals, key_bits, ko, vo, stream)
         return ko, vo
+
+
+class Graph:
+    """An executable CUDA graph captured by librogs; keeps its buffers alive."""
+
+    def __init__(self, handle, keep=()):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        R.rogs_graph_launch(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            R.rogs_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def zero_grads(m: SurfelTensors, exposure: torch.Tensor) -> dict:

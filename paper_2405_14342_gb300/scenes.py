@@ -66,8 +66,8 @@ class SurfelMap:
         return int(self.sem.shape[1])
 
     def copy(self) -> "SurfelMap":
-        return SurfelMap(*(np.array(getattr(self, f.name)) if isinstance(getattr(self, f.name), np.ndarray)
-                           else getattr(self, f.name) for f in dataclasses.fields(self)))
+        return SurfelMap(self.xyz.copy(), self.scale.copy(), self.quat.copy(), self.opacity.copy(),
+                         self.rgb.copy(), self.sem.copy(), tuple(self.grid_shape))
 
 
 @dataclasses.dataclass
@@ -247,7 +247,7 @@ def grid_road_map(C=19, seed=0, extent=2000.0, lane=3.5, spacing=0.1, roads=(0.0
     return _assemble(x, y, z, gx, gy, rng, C), field
 
 
-def intersection_camera(field, at=(1000.0, 1000.0), W=640, H=360, hfov=70.0, pitch=10.0, yaw=45.0):
+def intersection_camera(field, at=(1000.0, 1000.0), W=640, H=360, hfov=70.0, pitch=10.0, yaw=0.0):
     zg, _, _ = field(np.array([at[0]]), np.array([at[1]]))
     f = 0.5 * W / math.tan(math.radians(hfov / 2.0))
     return make_camera(PERSP, W, H, f, f, look_rotation(yaw, pitch), (at[0], at[1], float(zg[0]) + 1.5),

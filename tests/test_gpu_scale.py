@@ -1,0 +1,205 @@
+"""CUDA path vs the FP64 oracle at the workloads' full sizes, on sampled
+outputs, plus the equalities that must hold at any size:
+
+* scene config (1.6M surfels, 6 x 960x540): sampled pixels (road half and a
+  band of horizon rows, where tile lists are longest) at 1e-4;
+* batching config (48 views of uneven size in one call): every view equals
+  the same view rendered alone, bit for bit, and sampled pixels match the
+  oracle;
+* graph-captured step == eager step;
+* differentiation config (4.19M-surfel grid road network, 640x360): GPU
+  gradients of a loss on the 64x64 crop vs the FP64 reverse pass (1e-3
+  normwise) and vs central finite differences of the FP64 forward (eps 1e-4).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_14342_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from _util import gpu_pixels, gpu_state_T, normwise, pixel_index, planar_grad_from_pixels  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_14342_gb300 import render
+    return render
+
+
+@pytest.fixture(scope="module")
+def strip():
+    m, field = scenes.strip_map(C=19)
+    return m, field
+
+
+def sample_pixels(cams, n_per_view, seed, band=True):
+    rng = np.random.default_rng(seed)
+    out = []
+    for v, c in enumerate(cams):
+        u = rng.integers(0, c.width, n_per_view)
+        y = rng.integers(c.height // 2, c.height, n_per_view)
+        out.append(np.stack([np.full(n_per_view, v), u, y], -1))
+        if band:   # rows just below the horizon: the 40 m end of the box, longest lists
+            cy = int(c.cy)
+            yy, uu = np.meshgrid(np.arange(cy + 8, cy + 40, 4), np.arange(c.width // 2 - 64, c.width // 2 + 64, 8),
+                                 indexing="ij")
+            out.append(np.stack([np.full(uu.size, v), uu.ravel(), yy.ravel()], -1))
+    return np.ascontiguousarray(np.concatenate(out).astype(np.int32))
+
+
+def check_pixels(fr, C, ref, pix, depth_scale=40.0, tol=1e-4):
+    got = gpu_pixels(fr, C, pix)
+    ok = ref.amb == 0
+    assert (~ok).sum() <= max(4, 1e-3 * len(pix))
+    assert np.abs(got[ok, :3] - ref.out[ok, :3]).max() < tol
+    assert np.abs(got[ok, 3:3 + C] - ref.out[ok, 3:3 + C]).max() < tol
+    assert (np.abs(got[ok, 3 + C] - ref.out[ok, 3 + C]) / depth_scale).max() < tol
+    T = gpu_state_T(fr)[pixel_index(fr, pix)]
+    assert np.abs(T[ok] - ref.T[ok]).max() < tol
+
+
+def test_scene_config_sampled_pixels(R, strip):
+    m, field = strip
+    cams = scenes.surround_rig(field, 8)
+    ex = scenes.exposure_params(6)
+    rr = R.Renderer(19, record_capacity=2_000_000, pair_capacity=12_000_000)
+    st = R.SurfelTensors.from_map(m)
+    fr = rr.frame(cams)
+    rr.forward(st, fr, torch.as_tensor(ex, device="cuda"))
+    torch.cuda.synchronize()
+    cnt = rr.counts(fr)
+    assert cnt.n_records > 300_000 and cnt.n_pairs > 800_000
+    pix = sample_pixels(cams, 150, seed=1)
+    ref = oracle.render(m, cams, ex, pix)
+    assert (ref.T < 0.5).sum() > len(pix) // 3      # the sample does hit the road
+    check_pixels(fr, 19, ref, pix)
+
+
+def test_batching_config_matches_single_views_and_oracle(R, strip):
+    m, field = strip
+    cams = []
+    for t in range(8):
+        cams += scenes.surround_rig(field, 8 + 2 * t, sizes=scenes.BATCH_SIZES)
+    assert len(cams) == 48
+    ex = scenes.exposure_params(6)
+    ext = torch.as_tensor(ex, device="cuda")
+    st = R.SurfelTensors.from_map(m)
+    rr = R.Renderer(19, record_capacity=12_000_000, pair_capacity=60_000_000)
+    fr = rr.frame(cams)
+    rr.forward(st, fr, ext)
+    torch.cuda.synchronize()
+    rr.counts(fr)
+    Tb = gpu_state_T(fr)
+    r1 = R.Renderer(19, record_capacity=1_000_000, pair_capacity=6_000_000)
+    for v in (0, 1, 5, 17, 47):          # single-view renders are bit-identical
+        f1 = r1.frame([cams[v]])
+        r1.forward(st, f1, ext)
+        torch.cuda.synchronize()
+        r1.counts(f1)
+        assert torch.equal(f1.view(0, 19), fr.view(v, 19))
+        c = cams[v]
+        np.testing.assert_array_equal(gpu_state_T(f1), Tb[fr.pix_base[v]: fr.pix_base[v] + c.width * c.height])
+    sel = [0, 11, 23, 41]
+    pix = sample_pixels([cams[v] for v in sel], 60, seed=2, band=False)
+    pix_full = pix.copy()
+    pix_full[:, 0] = np.array(sel)[pix[:, 0]]
+    ref = oracle.render(m, cams, ex, pix_full)
+    check_pixels(fr, 19, ref, pix_full)
+
+
+def test_graph_replay_equals_eager_step(R):
+    m = scenes.tiny_map(C=8)
+    cams = [scenes.tiny_camera(), scenes.bev_camera((3.0, 3.0), 96, res_m=0.06, height_m=20.0)]
+    ex = torch.as_tensor(np.array([[0.05, 0.01]], np.float32), device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        rr = R.Renderer(8, record_capacity=1 << 16, pair_capacity=1 << 20)
+        st = R.SurfelTensors.from_map(m)
+        tg = scenes.random_targets(cams, 8, seed=9)
+        trgb, lab, msk = R.targets_to_device(tg)
+        fr_e = rr.frame(cams)
+        rr.forward(st, fr_e, ex)
+        loss_e, g_e = rr.loss(fr_e, trgb, lab, msk)
+        grads_e = rr.backward(st, fr_e, ex, g_e)
+        fr_g = rr.frame(cams)
+        loss_g = torch.empty(1, device="cuda")
+        gout_g = torch.empty_like(fr_g.out)
+        grads_g = R.zero_grads(st, ex)
+        graph = rr.train_graph(st, fr_g, ex, trgb, lab, msk, loss_g, gout_g, grads_g)
+        graph.launch()
+        s.synchronize()
+        assert torch.equal(fr_g.out, fr_e.out)
+        assert loss_g.item() == loss_e.item()
+        for k in grads_e:
+            assert normwise(grads_g[k].cpu().numpy(), grads_e[k].cpu().numpy()) < 1e-5, k
+        graph.launch()                     # replays accumulate into the gradients
+        s.synchronize()
+        assert normwise(grads_g["rgb"].cpu().numpy(), 2 * grads_e["rgb"].cpu().numpy()) < 1e-5
+        graph.close()
+
+
+def test_differentiation_config_crop_gradients(R):
+    m, field = scenes.grid_road_map(C=19)
+    assert 4_150_000 < m.n < 4_250_000
+    cam = scenes.intersection_camera(field)
+    cams = [cam]
+    ex = np.array([[0.02, -0.01]], np.float32)
+    pix = oracle.crop_pixels(0, 288, 296, 64, 64)          # rows 296-359, cols 288-351
+    rng = np.random.default_rng(4)
+    H, W = cam.height, cam.width
+    tg = scenes.Targets([rng.uniform(0, 1, (3, H, W)).astype(np.float32)],
+                        [rng.integers(0, 19, (H, W)).astype(np.int32)],
+                        [np.ones((H, W), np.uint8)])
+    ref = oracle.render(m, cams, ex, pix)
+    assert (ref.T < 0.5).mean() > 0.5                      # the crop sees road
+    rgb, lb, mk = oracle.gather_targets(tg, pix)
+    mk = mk * (ref.amb == 0)
+    L, gout = oracle.loss(ref.out, rgb, lb, mk, 19)
+    gref = oracle.backward(m, cams, ex, pix, gout)
+    rr = R.Renderer(19, record_capacity=2_000_000, pair_capacity=8_000_000)
+    st = R.SurfelTensors.from_map(m)
+    fr = rr.frame(cams)
+    ext = torch.as_tensor(ex, device="cuda")
+    rr.forward(st, fr, ext)
+    torch.cuda.synchronize()
+    rr.counts(fr)
+    check_pixels(fr, 19, ref, pix)
+    g = rr.backward(st, fr, ext, torch.as_tensor(planar_grad_from_pixels(fr, 19, pix, gout), device="cuda"))
+    torch.cuda.synchronize()
+    touched = np.nonzero(np.abs(gref.rgb).sum(1))[0]
+    assert len(touched) > 1000
+    for k in ("xyz", "scale", "quat", "opacity", "rgb", "sem", "exposure"):
+        a = g[k].cpu().numpy().astype(np.float64)
+        b = getattr(gref, k).reshape(a.shape)
+        assert normwise(a, b) < 1e-3, k
+    # central finite differences (eps 1e-4) of the FP64 forward, on a few parameters
+    sub = rng.choice(touched, 6, replace=False)
+    eps = 1e-4
+    rows = []
+    tg1 = scenes.Targets(tg.rgb, tg.label, [np.ones((H, W), np.uint8)])
+    pok = pix[ref.amb == 0]
+    base_sig = oracle.render(m, cams, ex, pok).sig
+    for i in sub:
+        for name, kk in (("xyz", 2), ("opacity", 0), ("scale", 0), ("rgb", 1)):
+            vals, flip = [], False
+            for d in (eps, -eps):
+                mp = m.copy()
+                arr = getattr(mp, name).astype(np.float64)
+                arr.reshape(m.n, -1)[i, kk] += d
+                setattr(mp, name, arr)
+                Lp, rp = oracle.loss_value(mp, cams, ex, tg1, pok)
+                flip |= not np.array_equal(rp.sig, base_sig)   # a composited list changed: discontinuity
+                vals.append(Lp)
+            if flip:
+                continue
+            fd = (vals[0] - vals[1]) / (2 * eps)
+            gpu = float(g[name].cpu().numpy().reshape(m.n, -1)[i, kk])
+            rows.append((fd, gpu))
+    assert len(rows) >= 16
+    fd = np.array([r[0] for r in rows]); gg = np.array([r[1] for r in rows])
+    assert np.abs(fd - gg).max() <= 2e-3 * np.abs(fd).max() + 1e-9
