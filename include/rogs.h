@@ -221,6 +221,73 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
 rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
                             int32_t key_bits, uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream);
 
+/* ---------------------------------------------------------- serving */
+
+/* A request loop that keeps one surfel map resident and renders incoming
+   BEV-orthographic and perspective requests (the paper's outputs: RGB,
+   semantic and elevation maps, Sec. 1 Fig. 1; BEV chunks per the
+   supplementary "Orthogonal Rendering Acceleration").  A worker thread takes
+   pending requests in arrival order into a batch (up to max_batch_views, as
+   long as the batch fits the free device memory), renders the whole batch in
+   one forward pass on one of max_inflight streams, packs each request's
+   channels and copies them to pinned host memory.  New batches are formed as
+   soon as a stream and memory free up, while earlier ones are still running
+   (continuous batching).  Each request's result does not depend on what it
+   was batched with. */
+typedef struct rogs_server rogs_server;
+
+enum { ROGS_CH_RGB = 1, ROGS_CH_SEM = 2, ROGS_CH_ELEV = 4 };
+
+typedef struct {
+    int32_t max_batch_views;   /* views per batched forward (1 = plain FIFO path) */
+    int32_t max_inflight;      /* batches in flight at once (one stream and context each) */
+    int32_t max_queue;         /* pending requests accepted before ROGS_ERR_BUSY */
+    int32_t reserved;
+    uint64_t memory_budget;    /* device bytes for in-flight batches (outputs + states + packed results) */
+    int64_t record_capacity;   /* per batch */
+    int64_t pair_capacity;     /* per batch */
+    double timeout_s;          /* a batch not finished after this long fails with ROGS_ERR_TIMEOUT */
+} rogs_serve_config;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches, views_rendered, pixels_rendered;
+    uint32_t pending, inflight;
+} rogs_serve_stats;
+
+/* Bytes of a request's packed result: for the requested channels, in this
+   order, RGB float32 [3][H][W] (after exposure), ELEV float32 [H][W], SEM
+   uint8 [H][W] (argmax of the composited logits).  ELEV is, for an
+   orthographic camera looking down, the world height of the composited
+   surface: camera z - D / (1 - T) (D = composited depth); for a perspective
+   camera the normalised depth D / (1 - T); NaN where 1 - T < 0.5. */
+rogs_status rogs_serve_result_bytes(const rogs_camera* cam, int32_t channels, int32_t num_classes, uint64_t* bytes);
+
+/* Start a server on the current device.  `cfg_render` gives the rendering
+   constants (tile, classes, thresholds; its capacities are replaced by those
+   of `cfg`).  The map (device pointers) and exposure [n_exposure,2] must stay
+   valid and unchanged until rogs_serve_close.  Allocates the device pool and
+   the contexts. */
+rogs_status rogs_serve_open(const rogs_config* cfg_render, const rogs_surfels* map, const float* exposure_ab,
+                            int32_t n_exposure, const rogs_serve_config* cfg, rogs_server** out);
+
+/* Queue one request (thread-safe).  ROGS_ERR_INVALID for a bad camera or
+   channel set, ROGS_ERR_OOM if the request alone can never fit the memory
+   budget, ROGS_ERR_BUSY if max_queue requests are already pending. */
+rogs_status rogs_serve_submit(rogs_server* srv, const rogs_camera* cam, int32_t channels, uint64_t* ticket);
+
+/* Non-blocking: if the request is finished, copy its packed result into
+   host_out (rogs_serve_result_bytes bytes), set *done = 1, forget the ticket
+   and return ROGS_OK; if not, set *done = 0 and return ROGS_ERR_NOT_READY.  A
+   failed request returns its error (ROGS_ERR_CAPACITY, ROGS_ERR_TIMEOUT,
+   ROGS_ERR_CUDA) once; an unknown ticket gives ROGS_ERR_INVALID. */
+rogs_status rogs_serve_poll(rogs_server* srv, uint64_t ticket, void* host_out, int32_t* done);
+
+rogs_status rogs_serve_get_stats(rogs_server* srv, rogs_serve_stats* out);
+
+/* Stop the worker, wait (bounded by timeout_s) for batches in flight, free
+   everything.  Unpolled results are dropped. */
+void rogs_serve_close(rogs_server* srv);
+
 /* ------------------------------------------------------ graph capture */
 
 typedef struct rogs_graph rogs_graph;

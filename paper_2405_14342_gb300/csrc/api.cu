@@ -323,10 +323,6 @@ rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
     ROGS_ALLOC(ctx->hist, radix_hist_words(big));
     ROGS_ALLOC(ctx->pair_off, R + 1);
     ROGS_ALLOC(ctx->pair_tiles, scan_tile_sums_words(R));
-    if (st == ROGS_OK) {
-        size_t cap_ = 0;
-        st = grow(ctx, ctx->rec_grad, cap_, R * (size_t)grad_channels(cfg->num_classes), nullptr, true);
-    }
     ROGS_ALLOC(ctx->loss_views, (size_t)kMaxViews);
 #undef ROGS_ALLOC
     (void)c0;
@@ -375,6 +371,15 @@ static rogs_status ensure_bits(rogs_ctx* ctx, long long n, int n_views, cudaStre
     }
     if (st == ROGS_OK) ctx->bits_cap = c1 < c2 ? c1 : c2;
     return st;
+}
+
+// The per-record gradient rows are only needed by the backward: allocated
+// (zeroed) on first use.
+static rogs_status ensure_rec_grad(rogs_ctx* ctx, cudaStream_t s) {
+    if (ctx->rec_grad) return ROGS_OK;
+    size_t cap = 0;
+    return grow(ctx, ctx->rec_grad, cap,
+                (size_t)ctx->cfg.record_capacity * (size_t)grad_channels(ctx->cfg.num_classes), s, true);
 }
 
 static rogs_status ensure_loss(rogs_ctx* ctx, long long total_pix, cudaStream_t s) {
@@ -560,6 +565,10 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
             return fail(ctx, ROGS_ERR_INVALID, "exposure_idx out of range");
     if (grads->quat && ((uintptr_t)grads->quat & 15u)) return fail(ctx, ROGS_ERR_INVALID, "grad quat alignment");
     cudaStream_t s = (cudaStream_t)stream;
+    {
+        rogs_status st = ensure_rec_grad(ctx, s);
+        if (st != ROGS_OK) return st;
+    }
     const rogs_state_layout L = layout_for(cfg, total_tiles, total_pix);
     const char* sb = (const char*)state;
     const StateHeader* hdr = (const StateHeader*)(sb + L.header);
@@ -630,6 +639,7 @@ static rogs_status begin_capture(rogs_ctx* ctx, const rogs_surfels* surfels, con
     if (!make_views(ctx->cfg, cams, n_views, va, tt, tp, err)) return fail(ctx, ROGS_ERR_INVALID, err);
     rogs_status st = ensure_bits(ctx, surfels->n, n_views, s);   // size scratch before capturing
     if (st == ROGS_OK && with_loss) st = ensure_loss(ctx, tp, s);
+    if (st == ROGS_OK && with_loss) st = ensure_rec_grad(ctx, s);
     if (st != ROGS_OK) return st;
     ROGS_CUDA(ctx, cudaStreamSynchronize(s));
     ROGS_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));

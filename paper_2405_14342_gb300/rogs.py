@@ -68,6 +68,21 @@ class rogs_state_layout(C.Structure):
                 ("total_pixels", C.c_int64)]
 
 
+class rogs_serve_config(C.Structure):
+    _fields_ = [("max_batch_views", C.c_int32), ("max_inflight", C.c_int32), ("max_queue", C.c_int32),
+                ("reserved", C.c_int32), ("memory_budget", C.c_uint64), ("record_capacity", C.c_int64),
+                ("pair_capacity", C.c_int64), ("timeout_s", C.c_double)]
+
+
+class rogs_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("batches", C.c_uint64), ("views_rendered", C.c_uint64), ("pixels_rendered", C.c_uint64),
+                ("pending", C.c_uint32), ("inflight", C.c_uint32)]
+
+
+ROGS_CH_RGB, ROGS_CH_SEM, ROGS_CH_ELEV = 1, 2, 4
+
+
 class rogs_profile(C.Structure):
     _fields_ = [("ms", C.c_double * 8), ("calls", C.c_uint64 * 8)]
 
@@ -112,11 +127,20 @@ def lib():
         L.rogs_graph_launch.argtypes = [P, P]
         L.rogs_graph_destroy.argtypes = [P]
         L.rogs_graph_destroy.restype = None
+        L.rogs_serve_result_bytes.argtypes = [C.POINTER(rogs_camera), C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]
+        L.rogs_serve_open.argtypes = [C.POINTER(rogs_config), C.POINTER(rogs_surfels), P, C.c_int32,
+                                      C.POINTER(rogs_serve_config), C.POINTER(P)]
+        L.rogs_serve_submit.argtypes = [P, C.POINTER(rogs_camera), C.c_int32, C.POINTER(C.c_uint64)]
+        L.rogs_serve_poll.argtypes = [P, C.c_uint64, P, C.POINTER(C.c_int32)]
+        L.rogs_serve_get_stats.argtypes = [P, C.POINTER(rogs_serve_stats)]
+        L.rogs_serve_close.argtypes = [P]
+        L.rogs_serve_close.restype = None
         L.rogs_profile_enable.argtypes = [P, C.c_int32]
         L.rogs_profile_read.argtypes = [P, C.POINTER(rogs_profile)]
         L.rogs_launch_count.argtypes = []
         L.rogs_launch_count.restype = C.c_uint64
-        for name in ("rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
+        for name in ("rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
+                     "rogs_serve_get_stats", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
                      "rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
                      "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
                      "rogs_render_bwd", "rogs_sort_pairs"):
@@ -281,3 +305,43 @@ def rogs_graph_launch(graph, stream=None):
 
 def rogs_graph_destroy(graph):
     lib().rogs_graph_destroy(graph)
+
+
+def rogs_serve_result_bytes(cam_arr, channels, num_classes) -> int:
+    b = C.c_uint64()
+    _check(None, lib().rogs_serve_result_bytes(cam_arr, int(channels), int(num_classes), C.byref(b)))
+    return int(b.value)
+
+
+def rogs_serve_open(cfg_render: rogs_config, surf: rogs_surfels, exposure_ab, cfg: rogs_serve_config):
+    h = C.c_void_p()
+    _check(None, lib().rogs_serve_open(C.byref(cfg_render), C.byref(surf), _ptr(exposure_ab),
+                                       int(exposure_ab.shape[0]), C.byref(cfg), C.byref(h)))
+    return h
+
+
+def rogs_serve_submit(srv, cam_arr, channels) -> int:
+    """Returns the ticket; raises RogsError (ROGS_ERR_BUSY / _OOM / _INVALID)."""
+    t = C.c_uint64()
+    _check(None, lib().rogs_serve_submit(srv, cam_arr, int(channels), C.byref(t)))
+    return int(t.value)
+
+
+def rogs_serve_poll(srv, ticket, host_buf) -> bool:
+    """True when finished (result copied into host_buf), False while not ready."""
+    d = C.c_int32()
+    st = lib().rogs_serve_poll(srv, C.c_uint64(ticket), host_buf, C.byref(d))
+    if st == ROGS_ERR_NOT_READY:
+        return False
+    _check(None, st)
+    return bool(d.value)
+
+
+def rogs_serve_get_stats(srv) -> rogs_serve_stats:
+    s = rogs_serve_stats()
+    _check(None, lib().rogs_serve_get_stats(srv, C.byref(s)))
+    return s
+
+
+def rogs_serve_close(srv):
+    lib().rogs_serve_close(srv)
