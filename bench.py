@@ -368,11 +368,107 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clocks,
     }
+    if not args.no_serve:
+        del frames, graphs, targets
+        torch.cuda.empty_cache()
+        line["serve"] = serve_bench(args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, rigs, budget_s=args.cpu_seconds)
     if world > 1:
         dist.destroy_process_group()
     return line
+
+
+# ---------------------------------------------------------------- serving
+
+def _percentile(x, q):
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+def serve_run(srv_factory, reqs, arrivals):
+    """Submit reqs at the given arrival times (s, relative), poll until all are
+    done; returns latencies (s) from arrival to result and the wall time."""
+    srv = srv_factory()
+    n = len(reqs)
+    lat = [None] * n
+    outstanding = {}
+    t0 = time.perf_counter()
+    i = 0
+    pix = 0
+    while i < n or outstanding:
+        now = time.perf_counter() - t0
+        while i < n and arrivals[i] <= now:
+            cam, ch = reqs[i]
+            outstanding[srv.submit(cam, ch)] = (i, arrivals[i])
+            pix += cam.width * cam.height
+            i += 1
+        done = []
+        for t, (k, arr) in outstanding.items():
+            if srv.poll(t) is not None:
+                lat[k] = time.perf_counter() - t0 - arr
+                done.append(t)
+        for t in done:
+            del outstanding[t]
+        if not done and i < n:
+            nxt = arrivals[i] - (time.perf_counter() - t0)
+            if nxt > 2e-4:
+                time.sleep(min(nxt - 1e-4, 1e-3))
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    return lat, wall, pix, stats
+
+
+def serve_bench(args):
+    """Serving config: 4.19M-surfel grid road map resident; 2000 Poisson-arrival
+    requests (BEV RGB/SEM/ELEV 256^2-2048^2 at 0.05 m/px, perspective
+    320x180-1920x1080); batched continuous serving vs the plain path (one view
+    per launch, FIFO), at 50% and 90% of the batched saturation rate."""
+    import torch
+    from paper_2405_14342_gb300 import render as R, rogs, scenes, serve
+    m, field = scenes.grid_road_map(C=19)
+    st = R.SurfelTensors.from_map(m)
+    n_surf = m.n
+    del m
+    ex = torch.zeros(1, 2, device="cuda")
+    reqs = scenes.serve_requests(field, n=args.serve_requests, seed=2)
+    cfg = rogs.rogs_default_config(19, 1 << 20, 1 << 22)
+    budget = int(args.serve_memory_gb * (1 << 30))
+
+    def batched():
+        return serve.Server(cfg, st, ex, max_batch_views=16, max_inflight=3, max_queue=1 << 20,
+                            memory_budget=budget, record_capacity=4_000_000, pair_capacity=24_000_000)
+
+    def plain():
+        return serve.Server(cfg, st, ex, max_batch_views=1, max_inflight=1, max_queue=1 << 20,
+                            memory_budget=budget, record_capacity=1_500_000, pair_capacity=8_000_000)
+
+    # warm up, then saturation (all requests at t = 0)
+    serve_run(batched, reqs[:50], np.zeros(50))
+    zero = np.zeros(len(reqs))
+    _, wall_b, pix_b, _ = serve_run(batched, reqs, zero)
+    _, wall_p, pix_p, _ = serve_run(plain, reqs, zero)
+    sat_b = len(reqs) / wall_b
+    sat_p = len(reqs) / wall_p
+    rng = np.random.default_rng(2)
+    out = {"workload": f"{n_surf} surfels (2x2 km grid road network, C=19) resident; {len(reqs)} requests, "
+                       "half BEV ortho 256^2-2048^2 at 0.05 m/px (RGB|SEM|ELEV), half perspective "
+                       "320x180-1920x1080 (RGB); Poisson arrivals",
+           "saturation": {"batched": {"req_s": round(sat_b, 1), "mpix_s": round(pix_b / wall_b / 1e6, 1)},
+                          "plain": {"req_s": round(sat_p, 1), "mpix_s": round(pix_p / wall_p / 1e6, 1)}},
+           "rates": []}
+    for frac in (0.5, 0.9):
+        lam = frac * sat_b
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, len(reqs)))
+        row = {"lambda_req_s": round(lam, 1), "of_batched_saturation": frac}
+        for name, fac in (("batched", batched), ("plain", plain)):
+            lat, wall, pix, stt = serve_run(fac, reqs, arrivals)
+            row[name] = {"p50_ms": round(_percentile(lat, 50) * 1e3, 3), "p99_ms": round(_percentile(lat, 99) * 1e3, 3),
+                         "mpix_s": round(pix / wall / 1e6, 1), "batches": int(stt.batches)}
+        out["rates"].append(row)
+    del st
+    torch.cuda.empty_cache()
+    return out
 
 
 # --------------------------------------------------------- CPU oracle arm
@@ -463,6 +559,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-memory-gb", type=float, default=24.0)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-pixels", type=int, default=200)
     ap.add_argument("--timesteps", type=int, default=T_COUNT, help="timesteps kept resident (profiling: fewer)")

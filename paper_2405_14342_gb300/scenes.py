@@ -311,3 +311,31 @@ def poses_on_trajectory(field, n=240, x0=100.0, speed=10.0, hz=12.0, y=20.0, rol
         out[k, :3] = (xt, y, float(zg[0]))
         out[k, 3:] = R.ravel()
     return out
+
+
+def serve_requests(field, n=2000, seed=2, roads=(0.0, 1000.0, 2000.0), extent=2000.0, res_m=0.05):
+    """Mixed serving requests over the grid road network: half BEV orthographic
+    tiles (side in {256, 512, 1024, 2048} px at res_m, channel set RGB, SEM or
+    ELEV) centred on a random road point, half perspective views ({320x180,
+    640x360, 1280x720, 1920x1080}, 70 deg HFOV, RGB) at a random road pose.
+    Returns a list of (Camera, channels) with channels 1 = RGB, 2 = SEM, 4 = ELEV."""
+    rng = np.random.default_rng(seed)
+    out = []
+    sizes = [(320, 180), (640, 360), (1280, 720), (1920, 1080)]
+    for i in range(n):
+        along = rng.uniform(50.0, extent - 50.0)
+        r = roads[rng.integers(0, len(roads))]
+        horizontal = rng.integers(0, 2) == 1           # road along x (y = r) or along y (x = r)
+        x, y = (along, r) if horizontal else (r, along)
+        zg, _, _ = field(np.array([x]), np.array([y]))
+        if i % 2 == 0:
+            side = int(rng.choice([256, 512, 1024, 2048]))
+            ch = int(rng.choice([1, 2, 4]))
+            out.append((bev_camera((x, y), side, res_m=res_m, height_m=100.0, ground_z=float(zg[0])), ch))
+        else:
+            W, H = sizes[rng.integers(0, 4)]
+            yaw = (0.0 if horizontal else 90.0) + (180.0 if rng.integers(0, 2) else 0.0) + rng.normal(0, 3.0)
+            f = 0.5 * W / math.tan(math.radians(35.0))
+            out.append((make_camera(PERSP, W, H, f, f, look_rotation(yaw, 0.0), (x, y, float(zg[0]) + 1.5),
+                                    use_box_cull=1), 1))
+    return out
