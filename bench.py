@@ -38,7 +38,11 @@ SM_COUNT, FP32_LANES = 152, 128   # GB300: 152 SMs x 128 FP32 lanes
 # Measured DRAM traffic (bytes per launch) of the dominant kernel from one ncu
 # capture, keyed by the sha256 of the source file it was taken from; a
 # different source hash means the kernel changed since and traffic is null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --set full, one launch of the scene workload (6 x 960x540, 16x16 tiles); see profiles/
+    "composite_bwd": {"bytes": 417_612_032 + 55_536_128, "sha": "d9836ece075a4108"},
+    "composite_fwd": {"bytes": 53_152_000 + 255_647_488, "sha": "e0fc030246e3acfb"},
+}
 
 
 def peaks():
