@@ -177,17 +177,28 @@ def run_ours(args):
     from paper_2405_14342_gb300 import render as R, rogs, scenes
 
     C = 19
-    tile = tuple(int(x) for x in args.tile.split("x"))
     n_t = args.timesteps
     m, field, rigs = build_workload(rank, C, world, n_t)
     stream = torch.cuda.Stream()          # graphs need a non-default stream
     torch.cuda.set_stream(stream)
     exposure = torch.as_tensor(scenes.exposure_params(6), device="cuda")
-    rr = R.Renderer(C, record_capacity=args.record_capacity, pair_capacity=args.pair_capacity, tile=tile)
-    rr.reserve(m.n, 6)
-    targets = make_targets(R, rr, scenes.perturb(m, seed=1), rigs, exposure)
+    r0 = R.Renderer(C, record_capacity=args.record_capacity, pair_capacity=args.pair_capacity)
+    targets = make_targets(R, r0, scenes.perturb(m, seed=1), rigs, exposure)
+    r0.close()
     st = R.SurfelTensors.from_map(m)
     del m
+    tuned = None
+    if args.tile == "auto":           # the autotuner picks tile shape and sort chunk (results never change)
+        from paper_2405_14342_gb300 import autotune
+        choice, timings = autotune.tune(st, rigs[:2], exposure, targets[:2], C, args.record_capacity,
+                                        args.pair_capacity, steps=6)
+        tile, sort_tile = choice["tile"], choice["sort_tile"]
+        tuned = {"choice": f"{tile[0]}x{tile[1]}/{sort_tile}", "ms_per_step": {k: round(v, 4) for k, v in timings.items()}}
+    else:
+        tile, sort_tile = tuple(int(x) for x in args.tile.split("x")), args.sort_tile
+    rr = R.Renderer(C, record_capacity=args.record_capacity, pair_capacity=args.pair_capacity, tile=tile,
+                    sort_tile=sort_tile)
+    rr.reserve(st.n, 6)
     frames = [rr.frame(c) for c in rigs]
     grads = R.zero_grads(st, exposure)
     P = frames[0].layout.total_pixels
@@ -246,7 +257,7 @@ def run_ours(args):
     if not args.no_plain:
         n_tp = min(n_t, 8)
         rp = R.Renderer(C, record_capacity=max(args.record_capacity // 4, 400_000),
-                        pair_capacity=max(args.pair_capacity // 4, 3_000_000), tile=tile)
+                        pair_capacity=max(args.pair_capacity // 4, 3_000_000), tile=tile, sort_tile=sort_tile)
         rp.reserve(st.n, 1)
         pframes, ptargets = [], []
         for k in range(n_tp):
@@ -352,7 +363,8 @@ def run_ours(args):
         "config": {"workload": "scene: 400x40 m strip, 0.1 m grid (1.6M surfels), C=19, 6x 960x540 surround "
                                "pinhole cams at 1.5 m, one fwd+loss+bwd per timestep (t=8..39)",
                    "surfels": st.n, "views_per_step": 6, "pixels_per_step": P, "classes": C,
-                   "tile": args.tile, "form": "batched (6 views per launch), CUDA-graph replay per timestep",
+                   "tile": f"{tile[0]}x{tile[1]}", "sort_tile": sort_tile, "autotune": tuned,
+                   "form": "batched (6 views per launch), CUDA-graph replay per timestep",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "timesteps_resident": n_t,
                    "l2": f"inputs larger than L2: 205 MB map + {n_t} timesteps of targets/outputs resident, "
@@ -557,7 +569,8 @@ def main():
     ap.add_argument("--steps", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="auto", help="auto (autotuner) or WxH")
+    ap.add_argument("--sort-tile", type=int, default=4096)
     ap.add_argument("--record-capacity", type=int, default=2_000_000)
     ap.add_argument("--pair-capacity", type=int, default=12_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -50,7 +50,8 @@ enum { ROGS_PERSP = 0, ROGS_ORTHO = 1 };
 
 /* Rendering constants.  Defaults (rogs_default_config): tile 16x16,
    t_min 1e-4, alpha_min 1/255, alpha_max 0.99, eps 0.3 px^2, near 0.2 m,
-   box 20 m / 40 m, jac_clamp 1.3. */
+   box 20 m / 40 m, jac_clamp 1.3, sort_tile 4096.  Tile shape and sort tile
+   only change speed, never results. */
 typedef struct {
     int32_t tile_w, tile_h;     /* 16x16, 32x8 or 8x8 pixels */
     int32_t num_classes;        /* C in [0, ROGS_MAX_CLASSES] */
@@ -62,6 +63,7 @@ typedef struct {
     float box_half_x;           /* perspective box cull: |lateral| <= box_half_x (m) */
     float box_depth;            /* and 0 <= forward <= box_depth (m) */
     float jac_clamp;            /* EWA Jacobian evaluated at x/z clamped to +-jac_clamp*W/(2 fx) */
+    int32_t sort_tile;          /* radix sort keys per CTA: 2048, 4096 (default) or 8192 */
     int64_t record_capacity;    /* visible (view, surfel) records per render call */
     int64_t pair_capacity;      /* (tile, record) pairs per render call (<= 2^32-1) */
 } rogs_config;
@@ -331,8 +333,8 @@ void rogs_graph_destroy(rogs_graph* graph);
    rogs_ctx.  Same result as rogs_sort_pairs: stable LSD radix sort of
    (key, value) pairs on key bits [0, key_bits); all pointers device; inputs
    are not modified; keys_out/vals_out must not overlap the inputs.
-   Scratch: a fixed array of 2 * ROGS_NOALLOC_MAX_PAIRS + 65792 uint32
-   (about 8.65 MB) compiled into the library's device image; every GPU that
+   Scratch: a fixed array of 2 * ROGS_NOALLOC_MAX_PAIRS + 131328 uint32
+   (about 8.9 MB) compiled into the library's device image; every GPU that
    loads the library holds it until the process exits.  The first call on a
    device looks the array's device address up (cudaGetSymbolAddress) and
    caches it: make that first call before any stream capture on that device.

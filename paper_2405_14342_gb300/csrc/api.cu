@@ -258,6 +258,10 @@ bool valid_config(const rogs_config& c, std::string& err) {
     }
     if (!(c.t_min > 0.0f) || !(c.t_min < 1.0f)) { err = "need 0 < t_min < 1"; return false; }
     if (!(c.eps_dilate >= 0.0f)) { err = "eps_dilate must be >= 0"; return false; }
+    if (c.sort_tile != 2048 && c.sort_tile != 4096 && c.sort_tile != 8192) {
+        err = "sort_tile must be 2048, 4096 or 8192";
+        return false;
+    }
     return true;
 }
 
@@ -294,6 +298,7 @@ rogs_status rogs_default_config(int32_t num_classes, int64_t record_capacity, in
     cfg->box_half_x = 20.0f;
     cfg->box_depth = 40.0f;
     cfg->jac_clamp = 1.3f;
+    cfg->sort_tile = 4096;
     cfg->record_capacity = record_capacity;
     cfg->pair_capacity = pair_capacity;
     return ROGS_OK;
@@ -501,20 +506,20 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
         // depth sort: stable on the binary32 depth key; ties keep (view, surfel) order
         prof_mark(ctx, 1, s);
         radix_sort_pairs(ctx->dk_a, ctx->dv_a, ctx->dk_b, ctx->dv_b, ctx->dk_c, ctx->dv_c, &hdr->n_records, rcap, 32,
-                         ctx->hist, s);
+                         ctx->hist, s, cfg.sort_tile);
         prof_mark(ctx, 2, s);
         scan_pairs(ctx->dv_b, rects, hdr, rcap, ctx->pair_off, ctx->pair_tiles, hdr, pcap, s);
         emit_pairs(views, ctx->dv_b, recs, rects, ctx->pair_off, hdr, rcap, ctx->pk_a, ctx->pv_a, pcap, s);
         // tile sort: stable on the global tile id; lists stay in depth order
         prof_mark(ctx, 3, s);
         radix_sort_pairs(ctx->pk_a, ctx->pv_a, ctx->pk_b, pair_rec, ctx->pk_c, ctx->pv_c, &hdr->n_pairs, pcap,
-                         bits_for(total_tiles), ctx->hist, s);
+                         bits_for(total_tiles), ctx->hist, s, cfg.sort_tile);
     }
     ROGS_CUDA(ctx, cudaMemsetAsync(ranges, 0, 8 * (size_t)total_tiles, s));
     if (n > 0) tile_ranges(ctx->pk_b, hdr, pcap, ranges, s);
     // longest lists first: the compositing kernels take their tiles in this order
     order_tiles(ranges, total_tiles, tile_order, (unsigned long long)total_tiles <= pcap, ctx->pk_a, ctx->pv_a,
-                ctx->pk_c, ctx->pv_c, ctx->pk_b, ctx->hist, s);
+                ctx->pk_c, ctx->pv_c, ctx->pk_b, ctx->hist, s, cfg.sort_tile);
     prof_mark(ctx, 4, s);
     composite_fwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
                   tile_order, exposure_ab, out, pix_T, pix_last, hdr, s);
@@ -603,7 +608,7 @@ rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32
     if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(ctx, ROGS_ERR_INVALID, "null device pointer");
     cudaStream_t s = (cudaStream_t)stream;
     radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, ctx->pk_c, ctx->pv_c, nullptr, (unsigned long long)n,
-                     key_bits, ctx->hist, s);
+                     key_bits, ctx->hist, s, ctx->cfg.sort_tile);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }

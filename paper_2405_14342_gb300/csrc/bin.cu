@@ -117,13 +117,14 @@ __global__ void __launch_bounds__(256) tile_keys_k(const uint2* __restrict__ ran
 }
 
 void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool sort_ok, uint32_t* ka, uint32_t* va,
-                 uint32_t* kb, uint32_t* vb, uint32_t* kalt, uint32_t* hist, cudaStream_t s) {
+                 uint32_t* kb, uint32_t* vb, uint32_t* kalt, uint32_t* hist, cudaStream_t s, int sort_tile) {
     long long blocks = (n_tiles + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
     tile_keys_k<<<(int)blocks, 256, 0, s>>>(ranges, n_tiles, ka, va, order, sort_ok ? 1 : 0);
     note_launches(1);
-    if (sort_ok) radix_sort_pairs(ka, va, kb, order, kalt, vb, nullptr, (unsigned long long)n_tiles, 16, hist, s);
+    if (sort_ok)
+        radix_sort_pairs(ka, va, kb, order, kalt, vb, nullptr, (unsigned long long)n_tiles, 16, hist, s, sort_tile);
 }
 
 }  // namespace rogs

@@ -26,7 +26,7 @@ struct GradPtrs {
 size_t radix_hist_words(unsigned long long cap);
 void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t* kalt,
                       uint32_t* valt, const unsigned long long* n_ptr, unsigned long long cap, int key_bits,
-                      uint32_t* hist, cudaStream_t s);
+                      uint32_t* hist, cudaStream_t s, int sort_tile = 4096);
 
 // ---- project.cu
 // Upload per-view parameters into device memory (by-value kernel argument).
@@ -57,7 +57,7 @@ void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t
 // Tile order by descending list length (identity when sort_ok is false);
 // uses ka/va/kb/vb/kalt (>= n_tiles uint32 each) and the radix histogram.
 void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool sort_ok, uint32_t* ka, uint32_t* va,
-                 uint32_t* kb, uint32_t* vb, uint32_t* kalt, uint32_t* hist, cudaStream_t s);
+                 uint32_t* kb, uint32_t* vb, uint32_t* kalt, uint32_t* hist, cudaStream_t s, int sort_tile);
 
 // ---- composite.cu
 int padded_channels(int C);

@@ -104,28 +104,28 @@ __global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restr
     }
 }
 
-// FP64 is slow on this part, so the partials are summed in FP32 with Kahan
-// compensation per thread and a fixed-order tree across threads.
-__global__ void __launch_bounds__(256) loss_final_k(const float* __restrict__ partials, int n,
-                                                    const unsigned long long* __restrict__ counter,
-                                                    float* __restrict__ loss) {
-    __shared__ float sh[256];
-    float s = 0.0f, comp = 0.0f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float y = partials[i] - comp;
-        const float t = s + y;
-        comp = (t - s) - y;
-        s = t;
-    }
-    sh[threadIdx.x] = s;
+// FP64 is slow on this part, so the partials are summed in FP32: each of
+// 1024 threads adds its strided share (loads unrolled so they overlap), then
+// a fixed-order tree; the result does not depend on timing.
+__global__ void __launch_bounds__(1024) loss_final_k(const float* __restrict__ partials, int n,
+                                                     const unsigned long long* __restrict__ counter,
+                                                     float* __restrict__ loss) {
+    __shared__ float sh[32];
+    float s = 0.0f;
+#pragma unroll 8
+    for (int i = threadIdx.x; i < n; i += 1024) s += partials[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const unsigned long long nm = *counter;
-        loss[0] = nm ? sh[0] / (float)nm : 0.0f;
+    if (threadIdx.x < 32) {
+        float t = sh[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+        if (threadIdx.x == 0) {
+            const unsigned long long nm = *counter;
+            loss[0] = nm ? t / (float)nm : 0.0f;
+        }
     }
 }
 
@@ -140,7 +140,7 @@ void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, 
     mask_count_k<<<gc, kLossThreads, 0, s>>>(mask, total_pixels, counter);
     loss_k<<<nb > 0 ? nb : 1, kLossThreads, 0, s>>>(views, n_views, total_pixels, C, out, tgt_rgb, label, mask,
                                                     lambda_c, lambda_s, counter, grad_out, partials);
-    loss_final_k<<<1, 256, 0, s>>>(partials, nb, counter, loss);
+    loss_final_k<<<1, 1024, 0, s>>>(partials, nb, counter, loss);
     note_launches(3);
     (void)n_blocks_cap;
 }

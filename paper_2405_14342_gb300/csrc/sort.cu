@@ -1,7 +1,9 @@
 // sort.cu -- hand-written stable LSD radix sort of (uint32 key, uint32 value)
 // pairs with a device-resident length (8-bit digits, 4096-key tiles).
 //
-// Per pass, three launches with fixed grids:
+// Keys per CTA (the sort "chunk") is 2048, 4096 or 8192 (8/16/32 keys per
+// thread), chosen by the context configuration.  Per pass, three launches
+// with fixed grids:
 //   rs_upsweep_k   per-tile digit histograms, digit-major [256][tiles]
 //   rs_rowscan_k   one block per digit: exclusive scan across tiles + digit total
 //   rs_downsweep_k stable scatter: the rank of a key inside its tile is built
@@ -18,17 +20,18 @@ namespace rogs {
 
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsIpt = 16;
-constexpr int kRsWarpItems = 32 * kRsIpt;
-constexpr int kRsTile = kRsThreads * kRsIpt;  // 4096 keys
+constexpr int kRsMinTile = 2048;   // smallest keys-per-CTA option (sizes the histograms)
 
 __device__ __forceinline__ unsigned long long rs_len(const unsigned long long* n_ptr, unsigned long long cap) {
     return scan_len(n_ptr, cap);
 }
 
+template <int IPT>
 __global__ void __launch_bounds__(kRsThreads) rs_upsweep_k(const uint32_t* __restrict__ keys,
                                                             const unsigned long long* n_ptr, unsigned long long cap,
                                                             int shift, uint32_t mask, uint32_t* __restrict__ hist) {
+    constexpr int kRsWarpItems = 32 * IPT;
+    constexpr int kRsTile = kRsThreads * IPT;
     __shared__ uint32_t sh[kRsWarps][256];
     const unsigned long long n = rs_len(n_ptr, cap);
     const unsigned ntiles = (unsigned)((n + kRsTile - 1) / kRsTile);
@@ -39,7 +42,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_k(const uint32_t* __res
         __syncthreads();
         const unsigned long long base = (unsigned long long)tile * kRsTile + (unsigned long long)warp * kRsWarpItems;
 #pragma unroll 4
-        for (int k = 0; k < kRsIpt; ++k) {
+        for (int k = 0; k < IPT; ++k) {
             unsigned long long i = base + k * 32 + lane;
             if (i < n) atomicAdd(&sh[warp][(keys[i] >> shift) & mask], 1u);
         }
@@ -55,10 +58,10 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_k(const uint32_t* __res
 // One block per digit: exclusive scan of hist[d][0..ntiles) in place.
 __global__ void __launch_bounds__(kScanThreads) rs_rowscan_k(uint32_t* __restrict__ hist,
                                                               const unsigned long long* n_ptr, unsigned long long cap,
-                                                              uint32_t* __restrict__ row_total) {
+                                                              int tile_keys, uint32_t* __restrict__ row_total) {
     __shared__ uint32_t sh[33];
     const unsigned long long n = rs_len(n_ptr, cap);
-    const unsigned ntiles = (unsigned)((n + kRsTile - 1) / kRsTile);
+    const unsigned ntiles = (unsigned)((n + tile_keys - 1) / tile_keys);
     uint32_t* row = hist + (unsigned long long)blockIdx.x * ntiles;
     uint32_t carry = 0;
     for (unsigned base = 0; base < ntiles; base += kScanThreads) {
@@ -72,12 +75,15 @@ __global__ void __launch_bounds__(kScanThreads) rs_rowscan_k(uint32_t* __restric
     if (threadIdx.x == 0) row_total[blockIdx.x] = carry;
 }
 
+template <int IPT>
 __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __restrict__ kin,
                                                               const uint32_t* __restrict__ vin,
                                                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                               const unsigned long long* n_ptr, unsigned long long cap,
                                                               int shift, uint32_t mask, const uint32_t* __restrict__ hist,
                                                               const uint32_t* __restrict__ row_total) {
+    constexpr int kRsWarpItems = 32 * IPT;
+    constexpr int kRsTile = kRsThreads * IPT;
     __shared__ uint32_t digit_base[256];
     __shared__ uint32_t wh[kRsWarps][256];
     __shared__ uint32_t scan_w[kRsWarps + 1];
@@ -111,9 +117,9 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __r
         for (int w = 0; w < kRsWarps; ++w) wh[w][threadIdx.x] = 0;
         __syncthreads();
         const unsigned long long base = (unsigned long long)tile * kRsTile + (unsigned long long)warp * kRsWarpItems;
-        uint32_t key[kRsIpt], val[kRsIpt], rank[kRsIpt];
+        uint32_t key[IPT], val[IPT], rank[IPT];
 #pragma unroll
-        for (int k = 0; k < kRsIpt; ++k) {
+        for (int k = 0; k < IPT; ++k) {
             unsigned long long i = base + k * 32 + lane;
             bool valid = i < n;
             key[k] = valid ? kin[i] : 0u;
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __r
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kRsIpt; ++k) {
+        for (int k = 0; k < IPT; ++k) {
             unsigned long long i = base + k * 32 + lane;
             if (i < n) {
                 uint32_t d = (key[k] >> shift) & mask;
@@ -167,40 +173,55 @@ __global__ void copy_pairs_k(const uint32_t* kin, const uint32_t* vin, uint32_t*
 }
 
 size_t radix_hist_words(unsigned long long cap) {
-    unsigned long long t = (cap + kRsTile - 1) / kRsTile;
+    unsigned long long t = (cap + kRsMinTile - 1) / kRsMinTile;
     if (t == 0) t = 1;
     return (size_t)(256 * t + 256);
 }
 
-void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t* kalt,
-                      uint32_t* valt, const unsigned long long* n_ptr, unsigned long long cap, int key_bits,
-                      uint32_t* hist, cudaStream_t s) {
-    uint32_t* row_total = hist + (radix_hist_words(cap) - 256);
-    int passes = (key_bits + 7) / 8;
-    unsigned long long tiles = (cap + kRsTile - 1) / kRsTile;
-    int grid = (int)(tiles < 1 ? 1 : (tiles > 2048 ? 2048 : tiles));
-    if (passes == 0) {
-        copy_pairs_k<<<grid, 256, 0, s>>>(kin, vin, kout, vout, n_ptr, cap);
-        note_launches(1);
-        return;
-    }
+template <int IPT>
+static void radix_passes(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t* kalt,
+                         uint32_t* valt, const unsigned long long* n_ptr, unsigned long long cap, int key_bits,
+                         uint32_t* hist, uint32_t* row_total, cudaStream_t s) {
+    constexpr int tile_keys = kRsThreads * IPT;
+    const int passes = (key_bits + 7) / 8;
+    unsigned long long tiles = (cap + tile_keys - 1) / tile_keys;
+    const int grid = (int)(tiles < 1 ? 1 : (tiles > 2048 ? 2048 : tiles));
     const uint32_t* sk = kin;
     const uint32_t* sv = vin;
     for (int p = 0; p < passes; ++p) {
         // the last pass must land in (kout, vout)
-        bool to_out = ((passes - 1 - p) % 2) == 0;
+        const bool to_out = ((passes - 1 - p) % 2) == 0;
         uint32_t* dk = to_out ? kout : kalt;
         uint32_t* dv = to_out ? vout : valt;
-        int shift = 8 * p;
-        int bits = key_bits - shift < 8 ? key_bits - shift : 8;
-        uint32_t mask = (bits >= 32) ? 0xffffffffu : ((1u << bits) - 1u);
-        rs_upsweep_k<<<grid, kRsThreads, 0, s>>>(sk, n_ptr, cap, shift, mask, hist);
-        rs_rowscan_k<<<256, kScanThreads, 0, s>>>(hist, n_ptr, cap, row_total);
-        rs_downsweep_k<<<grid, kRsThreads, 0, s>>>(sk, sv, dk, dv, n_ptr, cap, shift, mask, hist, row_total);
+        const int shift = 8 * p;
+        const int bits = key_bits - shift < 8 ? key_bits - shift : 8;
+        const uint32_t mask = (bits >= 32) ? 0xffffffffu : ((1u << bits) - 1u);
+        rs_upsweep_k<IPT><<<grid, kRsThreads, 0, s>>>(sk, n_ptr, cap, shift, mask, hist);
+        rs_rowscan_k<<<256, kScanThreads, 0, s>>>(hist, n_ptr, cap, tile_keys, row_total);
+        rs_downsweep_k<IPT><<<grid, kRsThreads, 0, s>>>(sk, sv, dk, dv, n_ptr, cap, shift, mask, hist, row_total);
         note_launches(3);
         sk = dk;
         sv = dv;
     }
+}
+
+void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t* kalt,
+                      uint32_t* valt, const unsigned long long* n_ptr, unsigned long long cap, int key_bits,
+                      uint32_t* hist, cudaStream_t s, int sort_tile) {
+    uint32_t* row_total = hist + (radix_hist_words(cap) - 256);
+    if ((key_bits + 7) / 8 == 0) {
+        unsigned long long blocks = (cap + 255) / 256;
+        const int grid = (int)(blocks < 1 ? 1 : (blocks > 2048 ? 2048 : blocks));
+        copy_pairs_k<<<grid, 256, 0, s>>>(kin, vin, kout, vout, n_ptr, cap);
+        note_launches(1);
+        return;
+    }
+    if (sort_tile == 2048)
+        radix_passes<8>(kin, vin, kout, vout, kalt, valt, n_ptr, cap, key_bits, hist, row_total, s);
+    else if (sort_tile == 8192)
+        radix_passes<32>(kin, vin, kout, vout, kalt, valt, n_ptr, cap, key_bits, hist, row_total, s);
+    else
+        radix_passes<16>(kin, vin, kout, vout, kalt, valt, n_ptr, cap, key_bits, hist, row_total, s);
 }
 
 }  // namespace rogs

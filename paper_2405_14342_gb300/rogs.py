@@ -34,7 +34,7 @@ class rogs_config(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("num_classes", C.c_int32),
                 ("t_min", C.c_float), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("eps_dilate", C.c_float), ("near_plane", C.c_float), ("box_half_x", C.c_float),
-                ("box_depth", C.c_float), ("jac_clamp", C.c_float),
+                ("box_depth", C.c_float), ("jac_clamp", C.c_float), ("sort_tile", C.c_int32),
                 ("record_capacity", C.c_int64), ("pair_capacity", C.c_int64)]
 
 

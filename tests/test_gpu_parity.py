@@ -71,10 +71,11 @@ def compare_forward(R, rr, m, cams, ex, depth_scale, max_band_frac=1e-4, max_ban
 
 # ---------------------------------------------------------------- sort
 
+@pytest.mark.parametrize("sort_tile", [2048, 4096, 8192])
 @pytest.mark.parametrize("n,bits", [(1, 32), (4095, 8), (4096, 18), (4097, 32), (123457, 18), (1 << 20, 32),
                                     (250001, 5)])
-def test_radix_sort_is_stable_and_exact(R, n, bits):
-    rr = make(R, 0, pairs=1 << 21)
+def test_radix_sort_is_stable_and_exact(R, n, bits, sort_tile):
+    rr = R.Renderer(0, record_capacity=1 << 10, pair_capacity=1 << 21, sort_tile=sort_tile)
     rng = np.random.default_rng(n)
     hi = (1 << bits) - 1
     keys = rng.integers(0, hi + 1, size=n, dtype=np.uint64).astype(np.uint32)
@@ -165,6 +166,23 @@ def test_forward_tiny_matches_oracle(R):
     for tile in [(16, 16), (32, 8), (8, 8)]:
         rr = make(R, m.num_classes, tile=tile)
         compare_forward(R, rr, m, [cam], np.array([[0.1, -0.03]], np.float32), depth_scale=[40.0])
+
+
+def test_schedule_choices_do_not_change_the_forward(R):
+    """Tile shape and sort chunk only reorder work: outputs are bit-identical."""
+    m = scenes.tiny_map(C=5)
+    cams = [scenes.tiny_camera(), scenes.bev_camera((3.0, 3.0), 77, res_m=0.05, height_m=20.0)]
+    ex = np.zeros((1, 2), np.float32)
+    ref = None
+    for tile in [(16, 16), (32, 8), (8, 8)]:
+        for st_ in (2048, 8192):
+            rr = R.Renderer(5, record_capacity=1 << 16, pair_capacity=1 << 20, tile=tile, sort_tile=st_)
+            st, fr, ext, cnt = gpu_render(R, rr, m, cams, ex)
+            out = fr.out.cpu().numpy()
+            if ref is None:
+                ref = out
+            else:
+                np.testing.assert_array_equal(out, ref)
 
 
 def test_forward_ragged_multiview_and_ortho(R):
