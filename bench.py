@@ -203,14 +203,11 @@ def run_ours(args):
     grads = R.zero_grads(st, exposure)
     P = frames[0].layout.total_pixels
     loss = torch.empty(1, device="cuda")
-    gout = torch.empty_like(frames[0].out)
 
     def step(k):
         fr = frames[k % n_t]
         trgb, lab, msk = targets[k % n_t]
-        rr.forward(st, fr, exposure)
-        rr.loss(fr, trgb, lab, msk, 1.0, 0.06, loss=loss, grad_out=gout)
-        rr.backward(st, fr, exposure, gout, grads=grads)
+        rr.train_step(st, fr, exposure, trgb, lab, msk, loss, grads)
 
     # set-up: every timestep's forward must fit the capacities (raises otherwise)
     for k in range(n_t):
@@ -223,7 +220,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- batched, graph-captured form (headline): one graph per timestep
-    graphs = [rr.train_graph(st, frames[k], exposure, *targets[k], loss, gout, grads) for k in range(n_t)]
+    graphs = [rr.train_graph(st, frames[k], exposure, *targets[k], loss, grads) for k in range(n_t)]
     for k in range(args.warmup):
         graphs[k % n_t].launch()
     torch.cuda.synchronize()
@@ -269,16 +266,12 @@ def run_ours(args):
                 ptargets.append((trgb[o3: o3 + 3 * npx], lab[o1: o1 + npx], msk[o1: o1 + npx]))
                 o3 += 3 * npx
                 o1 += npx
-        pgout = torch.empty_like(pframes[0].out)
-
         def step_plain(k):
             base = (k % n_tp) * 6
             for v in range(6):
                 fr = pframes[base + v]
                 a, b, c = ptargets[base + v]
-                rp.forward(st, fr, exposure)
-                rp.loss(fr, a, b, c, 1.0, 0.06, loss=loss, grad_out=pgout[: fr.out.numel()])
-                rp.backward(st, fr, exposure, pgout[: fr.out.numel()], grads=grads)
+                rp.train_step(st, fr, exposure, a, b, c, loss, grads)
 
         for k in range(n_tp):
             for v in range(6):

@@ -216,6 +216,18 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
                             int32_t n_views, const float* exposure_ab, int32_t n_exposure, const void* state,
                             const float* grad_out, const rogs_grads* grads, rogs_stream stream);
 
+/* One training step with the loss fused into the backward: rogs_render_fwd,
+   then the masked L1 + CE loss of rogs_loss and the backward of
+   rogs_render_bwd, except that dL/dout is computed inside the backward kernel
+   from `out` and the targets instead of being written to and read back from a
+   gradient image (same values as rogs_loss followed by rogs_render_bwd, up to
+   FP32 summation order).  Arguments as in those calls; gradients are ADDED
+   into `grads`; loss: device float[1]. */
+rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                            const float* exposure_ab, int32_t n_exposure, float* out, void* state,
+                            const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
+                            float lambda_s, float* loss, const rogs_grads* grads, rogs_stream stream);
+
 /* Stable LSD radix sort of (key, value) pairs of uint32 on key bits
    [0, key_bits) -- the sort used inside rogs_render_fwd, exposed for
    testing and reuse.  All pointers device; inputs are not modified; n <=
@@ -294,21 +306,20 @@ void rogs_serve_close(rogs_server* srv);
 
 typedef struct rogs_graph rogs_graph;
 
-/* Capture one training step -- rogs_render_fwd, rogs_loss and rogs_render_bwd
-   with exactly these arguments -- into a CUDA graph (the batched,
-   graph-captured form of the hot path: every view of the call is in each
-   stage's single launch, and replaying the graph removes the per-kernel
-   launch overhead).  All pointers are fixed in the graph; replays read the
-   current contents of the inputs and ADD into `grads` like rogs_render_bwd.
-   Scratch is sized before the capture starts (never during it).  `stream`
-   must not be the legacy default stream (NULL).  Argument errors are those of
-   the three calls.  On success *graph receives an executable graph owned by
-   the caller (free it with rogs_graph_destroy); ctx must outlive it. */
+/* Capture one training step -- rogs_train_step with exactly these arguments --
+   into a CUDA graph (the batched, graph-captured form of the hot path: every
+   view of the call is in each stage's single launch, and replaying the graph
+   removes the per-kernel launch overhead).  All pointers are fixed in the
+   graph; replays read the current contents of the inputs and ADD into
+   `grads`.  Scratch is sized before the capture starts (never during it).
+   `stream` must not be the legacy default stream (NULL).  Argument errors are
+   those of rogs_train_step.  On success *graph receives an executable graph
+   owned by the caller (free it with rogs_graph_destroy); ctx must outlive it. */
 rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
                                     int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
                                     void* state, const float* tgt_rgb, const int32_t* label, const uint8_t* mask,
-                                    float lambda_c, float lambda_s, float* loss, float* grad_out,
-                                    const rogs_grads* grads, rogs_stream stream, rogs_graph** graph);
+                                    float lambda_c, float lambda_s, float* loss, const rogs_grads* grads,
+                                    rogs_stream stream, rogs_graph** graph);
 
 /* Same, forward only (rogs_render_fwd). */
 rogs_status rogs_render_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,

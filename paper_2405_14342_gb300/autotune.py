@@ -33,14 +33,13 @@ def _time_candidate(m: R.SurfelTensors, frames_cams: List[list], exposure, targe
     try:
         frames = [rr.frame(c) for c in frames_cams]
         loss = torch.empty(1, device="cuda")
-        gout = torch.empty_like(frames[0].out)
         grads = R.zero_grads(m, exposure)
         for fr in frames:
             rr.forward(m, fr, exposure)
         torch.cuda.synchronize()
         for fr in frames:
             rr.counts(fr)
-        graphs = [rr.train_graph(m, fr, exposure, *tg, loss, gout, grads) for fr, tg in zip(frames, targets)]
+        graphs = [rr.train_graph(m, fr, exposure, *tg, loss, grads) for fr, tg in zip(frames, targets)]
         for g in graphs:
             g.launch()
         torch.cuda.synchronize()

@@ -383,12 +383,12 @@ static rogs_status ensure_bits(rogs_ctx* ctx, long long n, int n_views, cudaStre
 static rogs_status ensure_rec_grad(rogs_ctx* ctx, cudaStream_t s) {
     if (ctx->rec_grad) return ROGS_OK;
     size_t cap = 0;
-    return grow(ctx, ctx->rec_grad, cap,
-                (size_t)ctx->cfg.record_capacity * (size_t)grad_channels(ctx->cfg.num_classes), s, true);
+    return grow(ctx, ctx->rec_grad, cap, (size_t)ctx->cfg.record_capacity * (size_t)grad_channels(ctx->cfg.num_classes), s, true);
 }
 
-static rogs_status ensure_loss(rogs_ctx* ctx, long long total_pix, cudaStream_t s) {
-    const size_t nb = (size_t)loss_blocks(total_pix) + 1;
+static rogs_status ensure_loss(rogs_ctx* ctx, long long total_pix, cudaStream_t s, size_t min_partials = 0) {
+    size_t nb = (size_t)loss_blocks(total_pix) + 1;
+    if (min_partials + 1 > nb) nb = min_partials + 1;
     if (nb <= ctx->loss_cap && ctx->loss_partials) return ROGS_OK;
     size_t c = ctx->loss_cap, c2 = 0;
     rogs_status st = grow(ctx, ctx->loss_partials, c, nb, s);
@@ -588,12 +588,68 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     const SurfelPtrs sp{surfels->xyz, surfels->scale, surfels->quat, surfels->opacity, surfels->rgb, surfels->sem,
                         surfels->n};
     const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
+    BwdArgs a{};
+    a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs; a.pair_rec = pair_rec; a.ranges = ranges;
+    a.tile_order = tile_order; a.exposure_ab = exposure_ab; a.pix_T = pix_T; a.pix_last = pix_last;
+    a.grad_out = grad_out;
+    a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
     prof_mark(ctx, 6, s);
-    composite_bwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
-                  tile_order, exposure_ab, grad_out, pix_T, pix_last, ctx->rec_grad, grads->exposure, s);
+    composite_bwd(cfg.tile_w, cfg.tile_h, total_tiles, a, s);
     prof_mark(ctx, 7, s);
-    project_bwd(views, k, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp,
-                s);
+    project_bwd(views, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp, s);
+    prof_mark(ctx, -1, s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                            const float* exposure_ab, int32_t n_exposure, float* out, void* state,
+                            const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
+                            float lambda_s, float* loss, const rogs_grads* grads, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    const rogs_config& cfg = ctx->cfg;
+    if (!tgt_rgb || !mask || !loss || !grads || (cfg.num_classes > 0 && !label))
+        return fail(ctx, ROGS_ERR_INVALID, "null target/loss/grads pointer");
+    if (grads->quat && ((uintptr_t)grads->quat & 15u)) return fail(ctx, ROGS_ERR_INVALID, "grad quat alignment");
+    rogs_status st = rogs_render_fwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, stream);
+    if (st != ROGS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    static thread_local ViewsArg va;
+    long long total_tiles, total_pix;
+    std::string err;
+    make_views(cfg, cams, n_views, va, total_tiles, total_pix, err);   // validated by the forward
+    const int n_partials = bwd_loss_partials(total_tiles, cfg.tile_w, cfg.tile_h);
+    st = ensure_loss(ctx, total_pix, s, (size_t)n_partials);
+    if (st == ROGS_OK) st = ensure_rec_grad(ctx, s);
+    if (st != ROGS_OK) return st;
+    const rogs_state_layout L = layout_for(cfg, total_tiles, total_pix);
+    const char* sb = (const char*)state;
+    const StateHeader* hdr = (const StateHeader*)(sb + L.header);
+    const ViewParams* views = (const ViewParams*)(sb + L.views);
+    const Record* recs = (const Record*)(sb + L.records);
+    const Consts k = make_consts(cfg);
+    const SurfelPtrs sp{surfels->xyz, surfels->scale, surfels->quat, surfels->opacity, surfels->rgb, surfels->sem,
+                        surfels->n};
+    const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
+    prof_mark(ctx, 5, s);
+    mask_count(mask, total_pix, ctx->loss_counter, s);
+    BwdArgs a{};
+    a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs;
+    a.pair_rec = (const uint32_t*)(sb + L.pair_rec);
+    a.ranges = (const uint2*)(sb + L.tile_range);
+    a.tile_order = (const uint32_t*)(sb + L.tile_order);
+    a.exposure_ab = exposure_ab;
+    a.pix_T = (const float*)(sb + L.pix_T);
+    a.pix_last = (const uint32_t*)(sb + L.pix_last);
+    a.grad_out = nullptr;
+    a.out = out; a.tgt_rgb = tgt_rgb; a.label = label; a.mask = mask; a.mask_count = ctx->loss_counter;
+    a.lambda_c = lambda_c; a.lambda_s = lambda_s; a.loss_partials = ctx->loss_partials;
+    a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
+    prof_mark(ctx, 6, s);
+    composite_bwd(cfg.tile_w, cfg.tile_h, total_tiles, a, s);
+    loss_final(ctx->loss_partials, n_partials, ctx->loss_counter, loss, s);
+    prof_mark(ctx, 7, s);
+    project_bwd(views, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp, s);
     prof_mark(ctx, -1, s);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
@@ -643,7 +699,8 @@ static rogs_status begin_capture(rogs_ctx* ctx, const rogs_surfels* surfels, con
     std::string err;
     if (!make_views(ctx->cfg, cams, n_views, va, tt, tp, err)) return fail(ctx, ROGS_ERR_INVALID, err);
     rogs_status st = ensure_bits(ctx, surfels->n, n_views, s);   // size scratch before capturing
-    if (st == ROGS_OK && with_loss) st = ensure_loss(ctx, tp, s);
+    if (st == ROGS_OK && with_loss)
+        st = ensure_loss(ctx, tp, s, (size_t)bwd_loss_partials(tt, ctx->cfg.tile_w, ctx->cfg.tile_h));
     if (st == ROGS_OK && with_loss) st = ensure_rec_grad(ctx, s);
     if (st != ROGS_OK) return st;
     ROGS_CUDA(ctx, cudaStreamSynchronize(s));
@@ -654,18 +711,15 @@ static rogs_status begin_capture(rogs_ctx* ctx, const rogs_surfels* surfels, con
 rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
                                     int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
                                     void* state, const float* tgt_rgb, const int32_t* label, const uint8_t* mask,
-                                    float lambda_c, float lambda_s, float* loss, float* grad_out,
-                                    const rogs_grads* grads, rogs_stream stream, rogs_graph** gout) {
+                                    float lambda_c, float lambda_s, float* loss, const rogs_grads* grads,
+                                    rogs_stream stream, rogs_graph** gout) {
     if (!ctx || !gout) return ROGS_ERR_INVALID;
     *gout = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     rogs_status st = begin_capture(ctx, surfels, cams, n_views, s, true);
     if (st != ROGS_OK) return st;
-    st = rogs_render_fwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, stream);
-    if (st == ROGS_OK)
-        st = rogs_loss(ctx, cams, n_views, out, tgt_rgb, label, mask, lambda_c, lambda_s, loss, grad_out, stream);
-    if (st == ROGS_OK)
-        st = rogs_render_bwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, state, grad_out, grads, stream);
+    st = rogs_train_step(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, tgt_rgb, label, mask,
+                         lambda_c, lambda_s, loss, grads, stream);
     return finish_capture(ctx, s, st, gout);
 }
 

@@ -12,15 +12,20 @@
 // table; then each lane takes one entry and sums its gradient (mean 2, conic
 // 3, alpha 1, features 3 + C + 1) over the warp's pixels that received
 // anything (phase B, lane = entry), and the warp adds each entry's row to the
-// per-record gradient buffer with one coalesced atomic per channel.  Warps run
-// independently (no block barrier); a block holds two warps of one tile.
+// per-record gradient buffer with one coalesced atomic per column.
+// Warps run independently (no block barrier); a block holds two warps of one
+// tile.  For the fused training step the kernel computes dL/dout itself from
+// the forward output and the targets (masked L1 + CE), so no gradient image is
+// written or read, and leaves one loss partial per warp.
 //
-// project_bwd_k: one thread per record; chains the 2D gradients through the
+// project_bwd_k: one thread per record chains the 2D gradients through the
 // conic inverse, Sigma' = T2 T2^T + eps I, T2 = J W M, the perspective
 // Jacobian and mean, the quaternion normalisation and M = R[:, :2] diag(s),
 // and adds the per-surfel results (several views touch one surfel) with
-// atomics.  It clears each record's gradient row after reading it, so the
-// buffer is all zero again for the next backward.
+// atomics; then each warp walks its 32 records with lane = colour/semantic
+// column, so the feature gradients leave as coalesced atomics.  Every row is
+// cleared after it is read, so the buffer is all zero again for the next
+// backward.
 #include "kernels.h"
 
 namespace rogs {
@@ -48,20 +53,75 @@ __host__ __device__ constexpr int bwd_warp_floats() {
     return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 32 + 2 * 32 * kSubPad + NCP * kSubPad;
 }
 
+// dL/dout at one pixel, either read from grad_out or, for the fused training
+// step, computed from the forward output and the targets (Eqs. 8, 9, 12):
+//   dL/dc'  = lambda_c / |M| sign(c' - cbar)          (masked L1, three channels)
+//   dL/dsem = lambda_s / |M| (softmax(sem) - onehot)   (masked cross entropy)
+// Returns the pixel's unnormalised loss term lambda_c |c' - cbar|_1 + lambda_s CE.
+template <int NCP>
+__device__ __forceinline__ float pixel_grad(const BwdArgs& a, const ViewParams& v, int px, int py, int C, float (&G)[NCP]) {
+    const long long q = (long long)py * v.W + px;
+    const long long plane = (long long)v.W * v.H;
+    const int nch = 3 + C + 1;
+    if (!a.tgt_rgb) {
+        const float* go = a.grad_out + (long long)nch * v.pix_base + q;
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch) G[ch] = ch < nch ? go[ch * plane] : 0.0f;
+        return 0.0f;
+    }
+#pragma unroll
+    for (int ch = 0; ch < NCP; ++ch) G[ch] = 0.0f;
+    const long long pix = v.pix_base + q;
+    const unsigned long long nm = *a.mask_count;
+    if (!a.mask[pix] || nm == 0) return 0.0f;
+    const float inv = 1.0f / (float)nm;
+    const float* o = a.out + (long long)nch * v.pix_base + q;
+    const float* t = a.tgt_rgb + 3ll * v.pix_base + q;
+    float l1 = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float d = o[ch * plane] - t[ch * plane];
+        l1 += fabsf(d);
+        G[ch] = a.lambda_c * inv * (d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f));
+    }
+    float ce = 0.0f;
+    const int lb = C > 0 ? a.label[pix] : -1;
+    if (lb >= 0 && lb < C) {
+        float x[NCP];
+        float mx = -3.0e38f;
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch) {
+            x[ch] = (ch >= 3 && ch < 3 + C) ? o[ch * plane] : 0.0f;
+            if (ch >= 3 && ch < 3 + C) mx = fmaxf(mx, x[ch]);
+        }
+        float se = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch)
+            if (ch >= 3 && ch < 3 + C) se += expf(x[ch] - mx);
+        const float lse = mx + logf(se);
+        float xl = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch) {
+            if (ch >= 3 && ch < 3 + C) {
+                const bool hit = (ch - 3) == lb;
+                if (hit) xl = x[ch];
+                G[ch] = a.lambda_s * inv * (expf(x[ch] - lse) - (hit ? 1.0f : 0.0f));
+            }
+        }
+        ce = lse - xl;
+    }
+    return a.lambda_c * l1 + a.lambda_s * ce;
+}
+
 template <int TW, int TH, int NCP, int GP>
-__global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
-    const ViewParams* __restrict__ views, int n_views, Consts k, SurfelPtrs sp, const Record* __restrict__ recs,
-    const uint32_t* __restrict__ pair_rec, const uint2* __restrict__ ranges, const uint32_t* __restrict__ tile_order,
-    const float* __restrict__ exposure_ab,
-    const float* __restrict__ grad_out, const float* __restrict__ pix_T, const uint32_t* __restrict__ pix_last,
-    float* __restrict__ rec_grad, float* __restrict__ d_exposure) {
+__global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArgs a) {
     constexpr int WX = TW / 8;
     constexpr int NW = TW * TH / 32;
     constexpr int GROUPS = NW / kBwdWarpsPerBlock;
     constexpr int SP = kSubPad;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const long long tile = tile_order[blockIdx.x / GROUPS];
+    const long long tile = a.tile_order[blockIdx.x / GROUPS];
     const int warp = (int)(blockIdx.x % GROUPS) * kBwdWarpsPerBlock + wib;   // warp index inside the tile
     extern __shared__ float4 smem_bwd[];
     float* wbase = reinterpret_cast<float*>(smem_bwd) + wib * bwd_warp_floats<NCP>();
@@ -74,8 +134,10 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
     float* s_p = s_w + 32 * SP;
     float* s_G = s_p + 32 * SP;
 
-    const int vi = view_of_tile(views, n_views, tile);
-    const ViewParams& v = views[vi];
+    const Consts& k = a.k;
+    const SurfelPtrs& sp = a.sp;
+    const int vi = view_of_tile(a.views, a.n_views, tile);
+    const ViewParams& v = a.views[vi];
     const int W = v.W, H = v.H;
     const long long lt = tile - v.tile_base;
     const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
@@ -83,30 +145,34 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
     const int px = bx + (lane & 7), py = by + (lane >> 3);
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-    const uint32_t start = ranges[tile].x;
+    const uint32_t start = a.ranges[tile].x;
     const int C = k.C;
     const int nch = 3 + C + 1;
     const float amin = k.alpha_min, amax = k.alpha_max;
-    const float ea = expf(exposure_ab[2 * v.exp_idx]);
+    const float ea = expf(a.exposure_ab[2 * v.exp_idx]);
     const unsigned lt_mask = lanemask_lt();
 
     float T = 1.0f;
     uint32_t last = 0;
     float G[NCP];
-#pragma unroll
-    for (int ch = 0; ch < NCP; ++ch) G[ch] = 0.0f;
+    float lpix = 0.0f;
     float gsum_rgb = 0.0f;
     if (inside) {
-        const long long pix = v.pix_base + (long long)py * W + px;
-        const long long plane = (long long)W * H;
-        const float* go = grad_out + (long long)nch * v.pix_base + (long long)py * W + px;
-#pragma unroll
-        for (int ch = 0; ch < NCP; ++ch)
-            if (ch < nch) G[ch] = go[ch * plane];
+        lpix = pixel_grad<NCP>(a, v, px, py, C, G);
         gsum_rgb = G[0] + G[1] + G[2];
         G[0] *= ea; G[1] *= ea; G[2] *= ea;   // through c' = e^a c + b
-        T = pix_T[pix];
-        last = pix_last[pix];
+        const long long pix = v.pix_base + (long long)py * W + px;
+        T = a.pix_T[pix];
+        last = a.pix_last[pix];
+    } else {
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch) G[ch] = 0.0f;
+    }
+    if (a.loss_partials) {   // fused loss: one partial per warp, summed in a fixed order later
+        float l = lpix;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(kFull, l, o);
+        if (lane == 0) a.loss_partials[blockIdx.x * kBwdWarpsPerBlock + wib] = l;
     }
 #pragma unroll
     for (int ch = 0; ch < NCP; ++ch) s_G[ch * SP + lane] = G[ch];
@@ -123,8 +189,8 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
         if (j < cend) {
-            rec = pair_rec[start + j];
-            const float4* r4 = reinterpret_cast<const float4*>(recs + rec);
+            rec = a.pair_rec[start + j];
+            const float4* r4 = reinterpret_cast<const float4*>(a.recs + rec);
             m = r4[0];
             c = r4[1];
             hit = entry_hits_block(m, c, amin, (float)bx, (float)by);
@@ -139,7 +205,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
             s_c[slot] = c;
             s_rec[slot] = rec;
             s_idx[slot] = j;
-            const float4 d = reinterpret_cast<const float4*>(recs + rec)[2];
+            const float4 d = reinterpret_cast<const float4*>(a.recs + rec)[2];
             stage_features_bwd<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
         }
         __syncwarp();
@@ -153,11 +219,11 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
                 const float dx = pix_offset(pxc, mm.x, mm.z);
                 const float dy = pix_offset(pyc, mm.y, mm.w);
                 float g;
-                const float a = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
-                if (a >= amin) {
-                    const float oma = __fsub_rn(1.0f, a);
+                const float al = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
+                if (al >= amin) {
+                    const float oma = __fsub_rn(1.0f, al);
                     T = __fdiv_rn(T, oma);   // T_k
-                    w = a * T;
+                    w = al * T;
                     const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
                     float D = 0.0f;
 #pragma unroll
@@ -224,10 +290,10 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
         }
         const unsigned anym = __ballot_sync(kFull, any);
         __syncwarp();
-        // one coalesced atomic per (entry, channel)
+        // flush: one coalesced atomic per (entry, column) into the record's row
         for (unsigned q = anym; q; q &= q - 1) {
             const int e = __ffs(q) - 1;
-            float* dst = rec_grad + (unsigned long long)s_rec[e] * GP;
+            float* dst = a.rec_grad + (unsigned long long)s_rec[e] * GP;
             for (int col = lane; col < 6 + nch; col += 32) {
                 const float val = col < SP ? s_w[e * SP + col] : s_p[e * SP + col - SP];
                 if (val != 0.0f) atomicAdd(dst + col, val);
@@ -247,15 +313,19 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(
         e_a += __shfl_xor_sync(kFull, e_a, o);
         e_b += __shfl_xor_sync(kFull, e_b, o);
     }
-    if (lane == 0 && d_exposure) {
-        if (e_a != 0.0f) atomicAdd(&d_exposure[2 * v.exp_idx], e_a);
-        if (e_b != 0.0f) atomicAdd(&d_exposure[2 * v.exp_idx + 1], e_b);
+    if (lane == 0 && a.d_exposure) {
+        if (e_a != 0.0f) atomicAdd(&a.d_exposure[2 * v.exp_idx], e_a);
+        if (e_b != 0.0f) atomicAdd(&a.d_exposure[2 * v.exp_idx + 1], e_b);
     }
 }
 
 static size_t bwd_smem_bytes(int ncp) {
     return (size_t)kBwdWarpsPerBlock * 4 *
            (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 32 + 2 * 32 * kSubPad + ncp * kSubPad);
+}
+
+int bwd_loss_partials(long long total_tiles, int tile_w, int tile_h) {
+    return (int)(total_tiles * (tile_w * tile_h / 32));
 }
 
 template <int TW, int TH, int NCP, int GP>
@@ -283,19 +353,14 @@ void prepare_composite_bwd() {
 }
 
 template <int TW, int TH>
-static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
-                            Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                            const uint32_t* tile_order, const float* exposure_ab, const float* grad_out,
-                            const float* pix_T, const uint32_t* pix_last, float* rec_grad, float* d_exposure) {
+static void launch_bwd_tile(int ncp, long long total_tiles, const BwdArgs& a, cudaStream_t s) {
     constexpr int groups = TW * TH / 32 / kBwdWarpsPerBlock;
     dim3 grid((unsigned)(total_tiles * groups));
-#define ROGS_BWD(NCP, GP)                                                                                      \
-    do {                                                                                                       \
-        bwd_attr<TW, TH, NCP, GP>();                                                                           \
-        composite_bwd_k<TW, TH, NCP, GP><<<grid, 32 * kBwdWarpsPerBlock, bwd_smem_bytes(NCP), s>>>(            \
-            views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, grad_out, pix_T, pix_last, \
-            rec_grad, d_exposure);                                                                             \
-        note_launches(1);                                                                                      \
+#define ROGS_BWD(NCP, GP)                                                                           \
+    do {                                                                                            \
+        bwd_attr<TW, TH, NCP, GP>();                                                                \
+        composite_bwd_k<TW, TH, NCP, GP><<<grid, 32 * kBwdWarpsPerBlock, bwd_smem_bytes(NCP), s>>>(a); \
+        note_launches(1);                                                                           \
     } while (0)
     switch (ncp) {
         case 8: ROGS_BWD(8, 32); break;
@@ -308,52 +373,31 @@ static void launch_bwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
 #undef ROGS_BWD
 }
 
-void composite_bwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
-                   Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                   const uint32_t* tile_order, const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,
-                   float* rec_grad, float* d_exposure, cudaStream_t s) {
-    const int ncp = padded_channels(C);
-    if (tile_w == 32 && tile_h == 8)
-        launch_bwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab,
-                               grad_out, pix_T, pix_last, rec_grad, d_exposure);
-    else if (tile_w == 8 && tile_h == 8)
-        launch_bwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab,
-                              grad_out, pix_T, pix_last, rec_grad, d_exposure);
-    else
-        launch_bwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab,
-                                grad_out, pix_T, pix_last, rec_grad, d_exposure);
+void composite_bwd(int tile_w, int tile_h, long long total_tiles, const BwdArgs& a, cudaStream_t s) {
+    const int ncp = padded_channels(a.k.C);
+    if (tile_w == 32 && tile_h == 8) launch_bwd_tile<32, 8>(ncp, total_tiles, a, s);
+    else if (tile_w == 8 && tile_h == 8) launch_bwd_tile<8, 8>(ncp, total_tiles, a, s);
+    else launch_bwd_tile<16, 16>(ncp, total_tiles, a, s);
 }
 
 // ----------------------------------------------------------- project_bwd
 
-__global__ void __launch_bounds__(256) project_bwd_k(const ViewParams* __restrict__ views, Consts k, SurfelPtrs sp,
-                                                     const Record* __restrict__ recs,
-                                                     const StateHeader* __restrict__ hdr, unsigned long long rec_cap,
-                                                     float* __restrict__ rec_grad, int C, int GP, GradPtrs gp) {
-    unsigned long long n = hdr->n_records;
-    if (n > rec_cap) n = rec_cap;
-    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < n;
-         r += (unsigned long long)gridDim.x * blockDim.x) {
-        float* gr = rec_grad + r * (unsigned long long)GP;
-        const int used = 6 + 3 + C + 1;
-        bool any = false;
-        float g6[6];
-        for (int q = 0; q < 6; ++q) { g6[q] = gr[q]; any |= g6[q] != 0.0f; }
-        const Record rec = recs[r];
-        const uint32_t i = rec.surfel;
-        // features: rgb, sem, depth
-        float dz_feat = 0.0f;
-        for (int q = 6; q < used; ++q) {
-            const float val = gr[q];
-            if (val == 0.0f) continue;
-            gr[q] = 0.0f;
-            const int ch = q - 6;
-            if (ch < 3) { if (gp.rgb) atomicAdd(&gp.rgb[3ull * i + ch], val); }
-            else if (ch < 3 + C) { if (gp.sem) atomicAdd(&gp.sem[(unsigned long long)C * i + (ch - 3)], val); }
-            else { dz_feat = val; any = true; }
-        }
-        for (int q = 0; q < 6; ++q) gr[q] = 0.0f;
-        if (!any) continue;
+// Geometry part of one record's backward (row cols 0-5 and the depth column).
+__device__ __forceinline__ void project_bwd_record(const ViewParams* __restrict__ views, const SurfelPtrs& sp,
+                                                   const Record* __restrict__ recs, float* __restrict__ gr, int dcol,
+                                                   const GradPtrs& gp, unsigned long long r) {
+    const float4 ga = *reinterpret_cast<const float4*>(gr);
+    const float2 gb = *reinterpret_cast<const float2*>(gr + 4);
+    const float dz_feat = gr[dcol];   // depth-channel gradient
+    const float g6[6] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y};
+    const bool any = ga.x != 0.0f || ga.y != 0.0f || ga.z != 0.0f || ga.w != 0.0f || gb.x != 0.0f || gb.y != 0.0f ||
+                     dz_feat != 0.0f;
+    if (!any) return;
+    *reinterpret_cast<float4*>(gr) = make_float4(0.f, 0.f, 0.f, 0.f);   // leave the row zero for the next backward
+    *reinterpret_cast<float2*>(gr + 4) = make_float2(0.f, 0.f);
+    gr[dcol] = 0.0f;
+    const Record rec = recs[r];
+    const uint32_t i = rec.surfel;
         if (gp.opacity && g6[5] != 0.0f) atomicAdd(&gp.opacity[i], g6[5]);
 
         const ViewParams& v = views[rec.view];
@@ -467,15 +511,47 @@ __global__ void __launch_bounds__(256) project_bwd_k(const ViewParams* __restric
             atomicAdd(&gp.quat[4ull * i + 2], (dy_ - qy * dot) * invn);
             atomicAdd(&gp.quat[4ull * i + 3], (dz_ - qz * dot) * invn);
         }
+}
+
+__global__ void __launch_bounds__(256) project_bwd_k(const ViewParams* __restrict__ views, SurfelPtrs sp,
+                                                     const Record* __restrict__ recs,
+                                                     const StateHeader* __restrict__ hdr, unsigned long long rec_cap,
+                                                     float* __restrict__ rec_grad, int C, int GP, GradPtrs gp) {
+    unsigned long long n = hdr->n_records;
+    if (n > rec_cap) n = rec_cap;
+    const int lane = threadIdx.x & 31;
+    const int nf = 3 + C;                 // feature columns 6 .. 6 + nf - 1 (rgb, semantics)
+    const int dcol = 6 + nf;              // depth column
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long base = (blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32ull;
+         base < n; base += warps * 32ull) {
+        const unsigned long long r = base + lane;
+        uint32_t sid = 0;
+        if (r < n) {
+            sid = recs[r].surfel;
+            project_bwd_record(views, sp, recs, rec_grad + r * (unsigned long long)GP, dcol, gp, r);
+        }
+        const int cnt = n - base < 32ull ? (int)(n - base) : 32;
+        for (int j = 0; j < cnt; ++j) {
+            const uint32_t sj = __shfl_sync(kFull, sid, j);
+            float* row = rec_grad + (base + j) * (unsigned long long)GP + 6;
+            for (int c = lane; c < nf; c += 32) {
+                const float val = row[c];
+                if (val == 0.0f) continue;
+                row[c] = 0.0f;
+                if (c < 3) { if (gp.rgb) atomicAdd(&gp.rgb[3ull * sj + c], val); }
+                else if (gp.sem) atomicAdd(&gp.sem[(unsigned long long)C * sj + (c - 3)], val);
+            }
+        }
     }
 }
 
-void project_bwd(const ViewParams* views, Consts k, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
+void project_bwd(const ViewParams* views, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
                  unsigned long long rec_cap, float* rec_grad, int C, GradPtrs g, cudaStream_t s) {
     unsigned long long blocks = (rec_cap + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    project_bwd_k<<<(int)blocks, 256, 0, s>>>(views, k, sp, recs, hdr, rec_cap, rec_grad, C, grad_channels(C), g);
+    project_bwd_k<<<(int)blocks, 256, 0, s>>>(views, sp, recs, hdr, rec_cap, rec_grad, C, grad_channels(C), g);
     note_launches(1);
 }
 

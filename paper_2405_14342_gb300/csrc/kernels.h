@@ -68,13 +68,39 @@ void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n
                    cudaStream_t s);
 
 // ---- backward.cu
-int grad_channels(int C);  // per-record gradient stride (32 or 64)
+// per-record gradient row (32 or 64 floats): mean 2, conic 3, alpha, rgb 3, semantics C, depth
+int grad_channels(int C);
+
+struct BwdArgs {
+    const ViewParams* views;
+    int n_views;
+    Consts k;
+    SurfelPtrs sp;
+    const Record* recs;
+    const uint32_t* pair_rec;
+    const uint2* ranges;
+    const uint32_t* tile_order;
+    const float* exposure_ab;
+    const float* pix_T;
+    const uint32_t* pix_last;
+    // dL/dout: either grad_out, or (fused training step) computed from these
+    const float* grad_out;
+    const float* out;
+    const float* tgt_rgb;
+    const int32_t* label;
+    const uint8_t* mask;
+    const unsigned long long* mask_count;
+    float lambda_c, lambda_s;
+    float* loss_partials;   // one per warp of the launch, or null
+    // outputs
+    float* rec_grad;
+    float* d_exposure;
+};
+
 void prepare_composite_bwd();
-void composite_bwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
-                   Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
-                   const uint32_t* tile_order, const float* exposure_ab, const float* grad_out, const float* pix_T, const uint32_t* pix_last,
-                   float* rec_grad, float* d_exposure, cudaStream_t s);
-void project_bwd(const ViewParams* views, Consts k, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
+int bwd_loss_partials(long long total_tiles, int tile_w, int tile_h);
+void composite_bwd(int tile_w, int tile_h, long long total_tiles, const BwdArgs& a, cudaStream_t s);
+void project_bwd(const ViewParams* views, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
                  unsigned long long rec_cap, float* rec_grad, int C, GradPtrs g, cudaStream_t s);
 
 // ---- loss.cu
@@ -83,6 +109,8 @@ void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, 
                   float* loss, float* grad_out, unsigned long long* counter, float* partials, int n_blocks_cap,
                   cudaStream_t s);
 int loss_blocks(long long total_pixels);
+void mask_count(const uint8_t* mask, long long total_pixels, unsigned long long* counter, cudaStream_t s);
+void loss_final(const float* partials, int n, const unsigned long long* counter, float* loss, cudaStream_t s);
 
 // ---- init.cu
 void init_from_poses(const float* grid_xy, long long n, const float* poses_dev, long long n_poses, int exact_plane,

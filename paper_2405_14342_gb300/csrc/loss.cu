@@ -145,4 +145,18 @@ void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, 
     (void)n_blocks_cap;
 }
 
+void mask_count(const uint8_t* mask, long long total_pixels, unsigned long long* counter, cudaStream_t s) {
+    cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    long long nb = (total_pixels + kLossThreads - 1) / kLossThreads;
+    int gc = (int)(nb < 152 * 8 ? nb : 152 * 8);
+    if (gc < 1) gc = 1;
+    mask_count_k<<<gc, kLossThreads, 0, s>>>(mask, total_pixels, counter);
+    note_launches(1);
+}
+
+void loss_final(const float* partials, int n, const unsigned long long* counter, float* loss, cudaStream_t s) {
+    loss_final_k<<<1, 1024, 0, s>>>(partials, n, counter, loss);
+    note_launches(1);
+}
+
 }  // namespace rogs

@@ -148,15 +148,21 @@ class Renderer:
             setattr(g, k, t.data_ptr() if t is not None and t.numel() else None)
         return g
 
+    def train_step(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, tgt_rgb, label, mask,
+                   loss: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06, stream=None):
+        """Forward, masked L1 + CE loss and backward with the loss fused into the
+        backward kernel (rogs_train_step); gradients are added into `grads`."""
+        R.rogs_train_step(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out, frame.state,
+                          tgt_rgb, label, mask, lambda_c, lambda_s, loss, self.grads_struct(grads), stream)
+
     def train_graph(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, tgt_rgb, label, mask,
-                    loss: torch.Tensor, grad_out: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06,
-                    stream=None) -> "Graph":
-        """Capture forward + loss + backward of `frame` into a CUDA graph (all
-        pointers fixed; `stream` must be a non-default stream)."""
+                    loss: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06, stream=None) -> "Graph":
+        """Capture rogs_train_step of `frame` into a CUDA graph (all pointers
+        fixed; `stream` must be a non-default stream)."""
         g = R.rogs_train_graph_create(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
-                                      frame.state, tgt_rgb, label, mask, lambda_c, lambda_s, loss, grad_out,
+                                      frame.state, tgt_rgb, label, mask, lambda_c, lambda_s, loss,
                                       self.grads_struct(grads), stream)
-        return Graph(g, keep=(m, frame, exposure, tgt_rgb, label, mask, loss, grad_out, grads))
+        return Graph(g, keep=(m, frame, exposure, tgt_rgb, label, mask, loss, grads))
 
     def render_graph(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, stream=None) -> "Graph":
         g = R.rogs_render_graph_create(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,

@@ -120,8 +120,10 @@ def lib():
                                       P, P, C.POINTER(rogs_grads), P]
         L.rogs_sort_pairs.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P, P]
         L.rogs_train_graph_create.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P,
-                                              C.c_int32, P, P, P, P, P, C.c_float, C.c_float, P, P,
+                                              C.c_int32, P, P, P, P, P, C.c_float, C.c_float, P,
                                               C.POINTER(rogs_grads), P, C.POINTER(P)]
+        L.rogs_train_step.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
+                                      P, P, P, P, P, C.c_float, C.c_float, P, C.POINTER(rogs_grads), P]
         L.rogs_render_graph_create.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P,
                                                C.c_int32, P, P, P, C.POINTER(P)]
         L.rogs_graph_launch.argtypes = [P, P]
@@ -139,7 +141,7 @@ def lib():
         L.rogs_profile_read.argtypes = [P, C.POINTER(rogs_profile)]
         L.rogs_launch_count.argtypes = []
         L.rogs_launch_count.restype = C.c_uint64
-        for name in ("rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
+        for name in ("rogs_train_step", "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
                      "rogs_serve_get_stats", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
                      "rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
                      "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
@@ -282,13 +284,21 @@ def rogs_launch_count() -> int:
 
 
 def rogs_train_graph_create(ctx, surf, cam_arr, n_views, exposure_ab, out, state, tgt_rgb, label, mask, lambda_c,
-                            lambda_s, loss, grad_out, grads: rogs_grads, stream=None):
+                            lambda_s, loss, grads: rogs_grads, stream=None):
     g = C.c_void_p()
     _check(ctx, lib().rogs_train_graph_create(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
                                               int(exposure_ab.shape[0]), _ptr(out), _ptr(state), _ptr(tgt_rgb),
                                               _ptr(label), _ptr(mask), float(lambda_c), float(lambda_s), _ptr(loss),
-                                              _ptr(grad_out), C.byref(grads), _stream(stream), C.byref(g)))
+                                              C.byref(grads), _stream(stream), C.byref(g)))
     return g
+
+
+def rogs_train_step(ctx, surf, cam_arr, n_views, exposure_ab, out, state, tgt_rgb, label, mask, lambda_c, lambda_s,
+                    loss, grads: rogs_grads, stream=None):
+    _check(ctx, lib().rogs_train_step(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
+                                      int(exposure_ab.shape[0]), _ptr(out), _ptr(state), _ptr(tgt_rgb), _ptr(label),
+                                      _ptr(mask), float(lambda_c), float(lambda_s), _ptr(loss), C.byref(grads),
+                                      _stream(stream)))
 
 
 def rogs_render_graph_create(ctx, surf, cam_arr, n_views, exposure_ab, out, state, stream=None):

@@ -112,7 +112,10 @@ def test_batching_config_matches_single_views_and_oracle(R, strip):
     check_pixels(fr, 19, ref, pix_full)
 
 
-def test_graph_replay_equals_eager_step(R):
+def test_graph_replay_and_fused_step_equal_the_separate_calls(R):
+    """The fused training step (loss inside the backward) and its CUDA-graph
+    replay give the forward bit for bit and the loss and gradients of
+    rogs_render_fwd + rogs_loss + rogs_render_bwd up to FP32 summation order."""
     m = scenes.tiny_map(C=8)
     cams = [scenes.tiny_camera(), scenes.bev_camera((3.0, 3.0), 96, res_m=0.06, height_m=20.0)]
     ex = torch.as_tensor(np.array([[0.05, 0.01]], np.float32), device="cuda")
@@ -126,17 +129,24 @@ def test_graph_replay_equals_eager_step(R):
         rr.forward(st, fr_e, ex)
         loss_e, g_e = rr.loss(fr_e, trgb, lab, msk)
         grads_e = rr.backward(st, fr_e, ex, g_e)
+        # fused, eager
+        fr_f = rr.frame(cams)
+        loss_f = torch.empty(1, device="cuda")
+        grads_f = R.zero_grads(st, ex)
+        rr.train_step(st, fr_f, ex, trgb, lab, msk, loss_f, grads_f)
+        # fused, graph
         fr_g = rr.frame(cams)
         loss_g = torch.empty(1, device="cuda")
-        gout_g = torch.empty_like(fr_g.out)
         grads_g = R.zero_grads(st, ex)
-        graph = rr.train_graph(st, fr_g, ex, trgb, lab, msk, loss_g, gout_g, grads_g)
+        graph = rr.train_graph(st, fr_g, ex, trgb, lab, msk, loss_g, grads_g)
         graph.launch()
         s.synchronize()
-        assert torch.equal(fr_g.out, fr_e.out)
-        assert loss_g.item() == loss_e.item()
+        assert torch.equal(fr_g.out, fr_e.out) and torch.equal(fr_f.out, fr_e.out)
+        assert abs(loss_g.item() - loss_e.item()) <= 1e-6 * abs(loss_e.item())
+        assert abs(loss_f.item() - loss_e.item()) <= 1e-6 * abs(loss_e.item())
         for k in grads_e:
             assert normwise(grads_g[k].cpu().numpy(), grads_e[k].cpu().numpy()) < 1e-5, k
+            assert normwise(grads_f[k].cpu().numpy(), grads_e[k].cpu().numpy()) < 1e-5, k
         graph.launch()                     # replays accumulate into the gradients
         s.synchronize()
         assert normwise(grads_g["rgb"].cpu().numpy(), 2 * grads_e["rgb"].cpu().numpy()) < 1e-5
