@@ -50,7 +50,7 @@ constexpr int kBwdWarpsPerBlock = 2;
 
 template <int NCP>
 __host__ __device__ constexpr int bwd_warp_floats() {
-    return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 32 + 2 * 32 * kSubPad + NCP * kSubPad;
+    return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 32 + 2 * 32 * kSubPad + 32 * NCP;
 }
 
 // dL/dout at one pixel, either read from grad_out or, for the fused training
@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         if (lane == 0) a.loss_partials[blockIdx.x * kBwdWarpsPerBlock + wib] = l;
     }
 #pragma unroll
-    for (int ch = 0; ch < NCP; ++ch) s_G[ch * SP + lane] = G[ch];
+    for (int q = 0; q < NCP / 4; ++q)   // row per pixel: phase B reads it as broadcast float4s
+        reinterpret_cast<float4*>(s_G + lane * NCP)[q] = make_float4(G[4 * q], G[4 * q + 1], G[4 * q + 2], G[4 * q + 3]);
     const uint32_t wmax = __reduce_max_sync(kFull, last);
     __syncwarp();
 
@@ -221,20 +222,22 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
                 float g;
                 const float al = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
                 if (al >= amin) {
-                    const float oma = __fsub_rn(1.0f, al);
-                    T = __fdiv_rn(T, oma);   // T_k
+                    // 1 / (1 - alpha) off the loop-carried chain: only a multiply links T_k to T_{k+1}
+                    const float roma = __frcp_rn(__fsub_rn(1.0f, al));
+                    T = T * roma;   // T_k
                     w = al * T;
                     const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
-                    float D = 0.0f;
+                    float D0 = 0.0f, D1 = 0.0f, D2 = 0.0f, D3 = 0.0f;   // four short chains
 #pragma unroll
                     for (int q = 0; q < NCP / 4; ++q) {
                         const float4 f = f4[q];
-                        D = fmaf(G[4 * q], f.x, D);
-                        D = fmaf(G[4 * q + 1], f.y, D);
-                        D = fmaf(G[4 * q + 2], f.z, D);
-                        D = fmaf(G[4 * q + 3], f.w, D);
+                        D0 = fmaf(G[4 * q], f.x, D0);
+                        D1 = fmaf(G[4 * q + 1], f.y, D1);
+                        D2 = fmaf(G[4 * q + 2], f.z, D2);
+                        D3 = fmaf(G[4 * q + 3], f.w, D3);
                     }
-                    const float da = fmaf(T, D, -Ssum / oma);
+                    const float D = (D0 + D1) + (D2 + D3);
+                    const float da = fmaf(T, D, -Ssum * roma);
                     Ssum = fmaf(w, D, Ssum);
                     const float4 f0 = f4[0];
                     cr0 = fmaf(w, f0.x, cr0);
@@ -264,8 +267,15 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
                 const float w = s_w[e * SP + p];
                 if (w == 0.0f) continue;
                 any = true;
+                const float4* grow = reinterpret_cast<const float4*>(s_G + p * NCP);
 #pragma unroll
-                for (int ch = 0; ch < NCP; ++ch) acc[ch] = fmaf(w, s_G[ch * SP + p], acc[ch]);
+                for (int q = 0; q < NCP / 4; ++q) {
+                    const float4 gq = grow[q];
+                    acc[4 * q] = fmaf(w, gq.x, acc[4 * q]);
+                    acc[4 * q + 1] = fmaf(w, gq.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(w, gq.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(w, gq.w, acc[4 * q + 3]);
+                }
                 const float dpw = s_p[e * SP + p];
                 const float dx = pix_offset((float)(bx + (p & 7)) + 0.5f, mm.x, mm.z);
                 const float dy = pix_offset((float)(by + (p >> 3)) + 0.5f, mm.y, mm.w);
@@ -321,7 +331,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
 
 static size_t bwd_smem_bytes(int ncp) {
     return (size_t)kBwdWarpsPerBlock * 4 *
-           (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 32 + 2 * 32 * kSubPad + ncp * kSubPad);
+           (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 32 + 2 * 32 * kSubPad + 32 * ncp);
 }
 
 int bwd_loss_partials(long long total_tiles, int tile_w, int tile_h) {
