@@ -210,81 +210,89 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             stage_features_bwd<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
         }
         __syncwarp();
-        // phase A (lane = pixel): reverse recursion over the compacted entries
+        // phase A (lane = pixel): reverse recursion over the compacted entries.
+        // Branch-free: a lane whose entry does not count uses 1 / (1 - a) = 1 and
+        // w = 0, which leaves T and S unchanged, so iterations can overlap.
         unsigned pmask = 0;
+#pragma unroll 2
         for (int jj = h - 1; jj >= 0; --jj) {
-            float w = 0.0f, dpw = 0.0f;
-            if (s_idx[jj] < last) {
-                const float4 mm = s_m[jj];
-                const float4 cc = s_c[jj];
-                const float dx = pix_offset(pxc, mm.x, mm.z);
-                const float dy = pix_offset(pyc, mm.y, mm.w);
-                float g;
-                const float al = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
-                if (al >= amin) {
-                    // 1 / (1 - alpha) off the loop-carried chain: only a multiply links T_k to T_{k+1}
-                    const float roma = __frcp_rn(__fsub_rn(1.0f, al));
-                    T = T * roma;   // T_k
-                    w = al * T;
-                    const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
-                    float D0 = 0.0f, D1 = 0.0f, D2 = 0.0f, D3 = 0.0f;   // four short chains
+            const float4 mm = s_m[jj];
+            const float4 cc = s_c[jj];
+            const float dx = pix_offset(pxc, mm.x, mm.z);
+            const float dy = pix_offset(pyc, mm.y, mm.w);
+            float g;
+            const float al = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
+            const bool valid = s_idx[jj] < last && al >= amin;
+            // 1 / (1 - alpha) off the loop-carried chain: only a multiply links T_k to T_{k+1}
+            const float roma = valid ? __frcp_rn(__fsub_rn(1.0f, al)) : 1.0f;
+            T = T * roma;   // T_k
+            const float w = valid ? al * T : 0.0f;
+            const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
+            float D0 = 0.0f, D1 = 0.0f, D2 = 0.0f, D3 = 0.0f;   // four short chains
 #pragma unroll
-                    for (int q = 0; q < NCP / 4; ++q) {
-                        const float4 f = f4[q];
-                        D0 = fmaf(G[4 * q], f.x, D0);
-                        D1 = fmaf(G[4 * q + 1], f.y, D1);
-                        D2 = fmaf(G[4 * q + 2], f.z, D2);
-                        D3 = fmaf(G[4 * q + 3], f.w, D3);
-                    }
-                    const float D = (D0 + D1) + (D2 + D3);
-                    const float da = fmaf(T, D, -Ssum * roma);
-                    Ssum = fmaf(w, D, Ssum);
-                    const float4 f0 = f4[0];
-                    cr0 = fmaf(w, f0.x, cr0);
-                    cr1 = fmaf(w, f0.y, cr1);
-                    cr2 = fmaf(w, f0.z, cr2);
-                    const float ag = cc.w * g;
-                    if (ag < amax) dpw = da * ag;   // d alpha = dpw / alpha
-                }
+            for (int q = 0; q < NCP / 4; ++q) {
+                const float4 f = f4[q];
+                D0 = fmaf(G[4 * q], f.x, D0);
+                D1 = fmaf(G[4 * q + 1], f.y, D1);
+                D2 = fmaf(G[4 * q + 2], f.z, D2);
+                D3 = fmaf(G[4 * q + 3], f.w, D3);
             }
+            const float D = (D0 + D1) + (D2 + D3);
+            const float da = fmaf(T, D, -Ssum * roma);
+            Ssum = fmaf(w, D, Ssum);
+            const float4 f0 = f4[0];
+            cr0 = fmaf(w, f0.x, cr0);
+            cr1 = fmaf(w, f0.y, cr1);
+            cr2 = fmaf(w, f0.z, cr2);
+            const float ag = cc.w * g;
+            const float dpw = (valid && ag < amax) ? da * ag : 0.0f;   // d alpha = dpw / alpha
             s_w[jj * SP + lane] = w;
             s_p[jj * SP + lane] = dpw;
             pmask |= __ballot_sync(kFull, w != 0.0f);
         }
         __syncwarp();
-        // phase B (lane = entry): sum the entry's gradient over the pixels that got anything
+        // phase B (lane = entry): sum the entry's gradient over the pixels that got
+        // anything, two pixels per step and without branches (w = 0 adds nothing)
         bool any = false;
         if (lane < h) {
             const int e = lane;
             const float4 mm = s_m[e];
             const float4 cc = s_c[e];
+            // pixel offsets relative to the block's first pixel centre
+            const float dx0 = pix_offset((float)bx + 0.5f, mm.x, mm.z);
+            const float dy0 = pix_offset((float)by + 0.5f, mm.y, mm.w);
             float acc[NCP];
 #pragma unroll
             for (int ch = 0; ch < NCP; ++ch) acc[ch] = 0.0f;
             float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, g3 = 0.0f, g4 = 0.0f, g5 = 0.0f;
-            for (unsigned q = pmask; q; q &= q - 1) {
-                const int p = __ffs(q) - 1;
-                const float w = s_w[e * SP + p];
-                if (w == 0.0f) continue;
-                any = true;
-                const float4* grow = reinterpret_cast<const float4*>(s_G + p * NCP);
+            for (unsigned q = pmask; q;) {
+                const int p1 = __ffs(q) - 1;
+                q &= q - 1;
+                const int p2 = q ? __ffs(q) - 1 : p1;
+                const float w1 = s_w[e * SP + p1];
+                const float w2 = q ? s_w[e * SP + p2] : 0.0f;
+                const float dp1 = s_p[e * SP + p1];
+                const float dp2 = q ? s_p[e * SP + p2] : 0.0f;
+                q &= q - 1;
+                any |= (w1 != 0.0f) | (w2 != 0.0f);
+                const float4* r1 = reinterpret_cast<const float4*>(s_G + p1 * NCP);
+                const float4* r2 = reinterpret_cast<const float4*>(s_G + p2 * NCP);
 #pragma unroll
-                for (int q = 0; q < NCP / 4; ++q) {
-                    const float4 gq = grow[q];
-                    acc[4 * q] = fmaf(w, gq.x, acc[4 * q]);
-                    acc[4 * q + 1] = fmaf(w, gq.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(w, gq.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(w, gq.w, acc[4 * q + 3]);
+                for (int k4 = 0; k4 < NCP / 4; ++k4) {
+                    const float4 a1 = r1[k4], a2 = r2[k4];
+                    acc[4 * k4] = fmaf(w2, a2.x, fmaf(w1, a1.x, acc[4 * k4]));
+                    acc[4 * k4 + 1] = fmaf(w2, a2.y, fmaf(w1, a1.y, acc[4 * k4 + 1]));
+                    acc[4 * k4 + 2] = fmaf(w2, a2.z, fmaf(w1, a1.z, acc[4 * k4 + 2]));
+                    acc[4 * k4 + 3] = fmaf(w2, a2.w, fmaf(w1, a1.w, acc[4 * k4 + 3]));
                 }
-                const float dpw = s_p[e * SP + p];
-                const float dx = pix_offset((float)(bx + (p & 7)) + 0.5f, mm.x, mm.z);
-                const float dy = pix_offset((float)(by + (p >> 3)) + 0.5f, mm.y, mm.w);
-                g0 = fmaf(dpw, cc.x * dx + cc.y * dy, g0);
-                g1 = fmaf(dpw, cc.y * dx + cc.z * dy, g1);
-                g2 = fmaf(-0.5f * dpw, dx * dx, g2);
-                g3 = fmaf(-dpw, dx * dy, g3);
-                g4 = fmaf(-0.5f * dpw, dy * dy, g4);
-                g5 += dpw;
+                const float ax = dx0 + (float)(p1 & 7), ay = dy0 + (float)(p1 >> 3);
+                const float bxo = dx0 + (float)(p2 & 7), byo = dy0 + (float)(p2 >> 3);
+                g0 = fmaf(dp1, cc.x * ax + cc.y * ay, fmaf(dp2, cc.x * bxo + cc.y * byo, g0));
+                g1 = fmaf(dp1, cc.y * ax + cc.z * ay, fmaf(dp2, cc.y * bxo + cc.z * byo, g1));
+                g2 = fmaf(-0.5f * dp1, ax * ax, fmaf(-0.5f * dp2, bxo * bxo, g2));
+                g3 = fmaf(-dp1, ax * ay, fmaf(-dp2, bxo * byo, g3));
+                g4 = fmaf(-0.5f * dp1, ay * ay, fmaf(-0.5f * dp2, byo * byo, g4));
+                g5 += dp1 + dp2;
             }
             if (any) {   // the entry's row of the tables becomes its gradient row
                 float* r0 = s_w + e * SP;
