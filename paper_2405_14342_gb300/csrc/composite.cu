@@ -113,6 +113,9 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
         __syncwarp();
         const int h = __popc(mask);
         if (!done) {
+            // Entries below alpha_min add w = 0 (acc + 0 * f == acc exactly), so
+            // the only branch left is the transmittance stop.
+#pragma unroll 2
             for (int jj = 0; jj < h; ++jj) {
                 const float4 mm = s_m[jj];
                 const float4 cc = s_c[jj];
@@ -120,13 +123,13 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                 const float dy = pix_offset(pyc, mm.y, mm.w);
                 float g;
                 const float a = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
-                if (a < amin) continue;
+                const bool valid = a >= amin;
                 const float Tn = __fmul_rn(T, __fsub_rn(1.0f, a));
-                if (Tn < tmin) {
+                if (valid && Tn < tmin) {
                     done = true;
                     break;
                 }
-                const float w = __fmul_rn(a, T);
+                const float w = valid ? __fmul_rn(a, T) : 0.0f;
                 const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
 #pragma unroll
                 for (int q = 0; q < NCP / 4; ++q) {
@@ -136,9 +139,9 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                     acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
                     acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
                 }
-                T = Tn;
-                last = s_idx[jj];
-                ++ncomp;
+                T = valid ? Tn : T;
+                last = valid ? s_idx[jj] : last;
+                ncomp += valid ? 1u : 0u;
             }
         }
         __syncwarp();
