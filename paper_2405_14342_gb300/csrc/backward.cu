@@ -50,7 +50,7 @@ constexpr int kBwdWarpsPerBlock = 2;
 
 template <int NCP>
 __host__ __device__ constexpr int bwd_warp_floats() {
-    return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 32 + 2 * 32 * kSubPad + 32 * NCP;
+    return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 32 + 2 * 32 * kSubPad;
 }
 
 // dL/dout at one pixel, either read from grad_out or, for the fused training
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     uint32_t* s_idx = s_rec + 32;
     float* s_w = reinterpret_cast<float*>(s_idx + 32);
     float* s_p = s_w + 32 * SP;
-    float* s_G = s_p + 32 * SP;
+    float* s_G = s_f;   // dL/dout rows per pixel, written over the features once phase A is done
 
     const Consts& k = a.k;
     const SurfelPtrs& sp = a.sp;
@@ -174,9 +174,6 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(kFull, l, o);
         if (lane == 0) a.loss_partials[blockIdx.x * kBwdWarpsPerBlock + wib] = l;
     }
-#pragma unroll
-    for (int q = 0; q < NCP / 4; ++q)   // row per pixel: phase B reads it as broadcast float4s
-        reinterpret_cast<float4*>(s_G + lane * NCP)[q] = make_float4(G[4 * q], G[4 * q + 1], G[4 * q + 2], G[4 * q + 3]);
     const uint32_t wmax = __reduce_max_sync(kFull, last);
     __syncwarp();
 
@@ -250,6 +247,10 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             s_p[jj * SP + lane] = dpw;
             pmask |= __ballot_sync(kFull, w != 0.0f);
         }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NCP / 4; ++q)   // row per pixel: phase B reads it as broadcast float4s
+            reinterpret_cast<float4*>(s_G + lane * NCP)[q] = make_float4(G[4 * q], G[4 * q + 1], G[4 * q + 2], G[4 * q + 3]);
         __syncwarp();
         // phase B (lane = entry): sum the entry's gradient over the pixels that got
         // anything, two pixels per step and without branches (w = 0 adds nothing)
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
 
 static size_t bwd_smem_bytes(int ncp) {
     return (size_t)kBwdWarpsPerBlock * 4 *
-           (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 32 + 2 * 32 * kSubPad + 32 * ncp);
+           (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 32 + 2 * 32 * kSubPad);
 }
 
 int bwd_loss_partials(long long total_tiles, int tile_w, int tile_h) {
