@@ -50,7 +50,7 @@ constexpr int kBwdWarpsPerBlock = 2;
 
 template <int NCP>
 __host__ __device__ constexpr int bwd_warp_floats() {
-    return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 32 + 2 * 32 * kSubPad;
+    return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 2 * 32 * kSubPad;
 }
 
 // dL/dout at one pixel, either read from grad_out or, for the fused training
@@ -129,8 +129,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     float4* s_c = s_m + 32;
     float* s_f = reinterpret_cast<float*>(s_c + 32);
     uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_f + 32 * NCP);
-    uint32_t* s_idx = s_rec + 32;
-    float* s_w = reinterpret_cast<float*>(s_idx + 32);
+    float* s_w = reinterpret_cast<float*>(s_rec + 32);
     float* s_p = s_w + 32 * SP;
     float* s_G = s_f;   // dL/dout rows per pixel, written over the features once phase A is done
 
@@ -202,7 +201,6 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             s_m[slot] = m;
             s_c[slot] = c;
             s_rec[slot] = rec;
-            s_idx[slot] = j;
             const float4 d = reinterpret_cast<const float4*>(a.recs + rec)[2];
             stage_features_bwd<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
         }
@@ -211,6 +209,9 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         // Branch-free: a lane whose entry does not count uses 1 / (1 - a) = 1 and
         // w = 0, which leaves T and S unchanged, so iterations can overlap.
         unsigned pmask = 0;
+        // entries this pixel composited: list index < last, a prefix of the compacted slots
+        const int rel = (int)last - (int)cbeg;
+        const int kmax = rel <= 0 ? 0 : __popc(rel >= 32 ? mask : (mask & ((1u << rel) - 1u)));
 #pragma unroll 2
         for (int jj = h - 1; jj >= 0; --jj) {
             const float4 mm = s_m[jj];
@@ -219,9 +220,10 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             const float dy = pix_offset(pyc, mm.y, mm.w);
             float g;
             const float al = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
-            const bool valid = s_idx[jj] < last && al >= amin;
+            const bool valid = jj < kmax && al >= amin;
             // 1 / (1 - alpha) off the loop-carried chain: only a multiply links T_k to T_{k+1}
-            const float roma = valid ? __frcp_rn(__fsub_rn(1.0f, al)) : 1.0f;
+            // (1 - alpha >= 0.01, so the fast reciprocal is within 2 ulp)
+            const float roma = valid ? __fdividef(1.0f, __fsub_rn(1.0f, al)) : 1.0f;
             T = T * roma;   // T_k
             const float w = valid ? al * T : 0.0f;
             const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
 
 static size_t bwd_smem_bytes(int ncp) {
     return (size_t)kBwdWarpsPerBlock * 4 *
-           (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 32 + 2 * 32 * kSubPad);
+           (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 2 * 32 * kSubPad);
 }
 
 int bwd_loss_partials(long long total_tiles, int tile_w, int tile_h) {
