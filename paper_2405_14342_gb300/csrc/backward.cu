@@ -32,19 +32,6 @@ namespace rogs {
 
 int grad_channels(int C) { return padded_channels(C) <= 24 ? 32 : 64; }
 
-template <int NCP>
-__device__ __forceinline__ void stage_features_bwd(float* f, uint32_t s, float depth, const SurfelPtrs& sp, int C) {
-    f[0] = sp.rgb[3ull * s];
-    f[1] = sp.rgb[3ull * s + 1];
-    f[2] = sp.rgb[3ull * s + 2];
-    const float* sem = sp.sem + (unsigned long long)C * s;
-    for (int ch = 0; ch < C; ++ch) f[3 + ch] = sem[ch];
-    f[3 + C] = depth;
-#pragma unroll
-    for (int ch = 0; ch < NCP; ++ch)
-        if (ch > 3 + C) f[ch] = 0.0f;
-}
-
 constexpr int kSubPad = 33;   // padded row stride of the per-warp tables
 constexpr int kBwdWarpsPerBlock = 2;
 
@@ -202,7 +189,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             s_c[slot] = c;
             s_rec[slot] = rec;
             const float4 d = reinterpret_cast<const float4*>(a.recs + rec)[2];
-            stage_features_bwd<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
+            stage_surfel_features<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
         }
         __syncwarp();
         // phase A (lane = pixel): reverse recursion over the compacted entries.
@@ -363,7 +350,7 @@ static void bwd_attr() {
 
 template <int TW, int TH>
 static void prepare_bwd_tile() {
-    bwd_attr<TW, TH, 8, 32>(); bwd_attr<TW, TH, 12, 32>(); bwd_attr<TW, TH, 16, 32>();
+    bwd_attr<TW, TH, 8, 32>(); bwd_attr<TW, TH, 16, 32>();
     bwd_attr<TW, TH, 24, 32>(); bwd_attr<TW, TH, 32, 64>(); bwd_attr<TW, TH, 64, 64>();
 }
 
@@ -385,7 +372,6 @@ static void launch_bwd_tile(int ncp, long long total_tiles, const BwdArgs& a, cu
     } while (0)
     switch (ncp) {
         case 8: ROGS_BWD(8, 32); break;
-        case 12: ROGS_BWD(12, 32); break;
         case 16: ROGS_BWD(16, 32); break;
         case 24: ROGS_BWD(24, 32); break;
         case 32: ROGS_BWD(32, 64); break;

@@ -158,15 +158,55 @@ __device__ __forceinline__ float surfel_alpha(float dx, float dy, float A, float
 // Conservative test: can the entry reach a >= alpha_min at some pixel centre
 // of the 8x4 block whose first pixel is (bx, by)?  Uses the bounding box of
 // the ellipse d^T Q d <= 2 ln(alpha / alpha_min) (Q = conic), padded so that
-// binary32 rounding never drops a pixel the exact per-pixel test would keep.
+// rounding never drops a pixel the exact per-pixel test would keep: the fast
+// log, divisions and reciprocal square root used here are within a few ulp,
+// far inside the 0.2 % + 0.01 px margin.
 __device__ __forceinline__ bool entry_hits_block(float4 m, float4 c, float alpha_min, float bx, float by) {
     const float det = c.x * c.z - c.y * c.y;
     if (!(det > 0.0f)) return true;   // degenerate: keep
-    const float kap = fmaxf(2.0f * logf(c.w / alpha_min), 0.0f);
-    const float rx = sqrtf(kap * c.z / det) * 1.002f + 0.01f;
-    const float ry = sqrtf(kap * c.x / det) * 1.002f + 0.01f;
+    const float kap = __fdividef(fmaxf(2.0f * __logf(__fdividef(c.w, alpha_min)), 0.0f), det);
+    const float qx = fmaxf(kap * c.z, 1e-30f), qy = fmaxf(kap * c.x, 1e-30f);
+    const float rx = qx * rsqrtf(qx) * 1.002f + 0.01f;
+    const float ry = qy * rsqrtf(qy) * 1.002f + 0.01f;
     const float mx = m.x + m.z, my = m.y + m.w;
     return (mx + rx >= bx + 0.5f) && (mx - rx <= bx + 7.5f) && (my + ry >= by + 0.5f) && (my - ry <= by + 3.5f);
+}
+
+// ------------------------------------------------------------ tensor cores
+// Warp-level m16n8k8 TF32 MMA with FP32 accumulation.  Fragment layout (PTX
+// ISA, mma m16n8k8 .tf32), g = lane / 4, t = lane % 4:
+//   A (16x8, row): a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
+//   B (8x8, col):  b0 (t, g), b1 (t+4, g)
+//   C (16x8):      c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+// Products are taken in three TF32 passes (a_hi b_hi + a_hi b_lo + a_lo b_hi,
+// x = hi + lo with hi = x rounded to TF32 and lo = x - hi exactly), which
+// keeps them to about FP32 accuracy.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// d += A B in three TF32 passes; ah/al, bh/bl are the split fragments.
+__device__ __forceinline__ void mma_tf32x3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                           const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+    mma_tf32(d, al[0], al[1], al[2], al[3], bh[0], bh[1]);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -11,39 +11,37 @@
 // whose footprint can reach the warp's block (a conservative ellipse
 // bounding box), compact them in order into the warp's shared-memory slots
 // together with their features (rgb, sem, depth), and then every lane walks
-// the compacted entries for its pixel.  A warp stops as soon as all its
-// pixels have stopped (transmittance stop), without waiting for the rest of
-// the tile: there is no block-wide barrier.
+// the compacted entries for its pixel, computing only the scalar recursion
+// (alpha, the transmittance stop, w = a T) and writing its weights into a
+// (entry x pixel) table.  The channel sums of Eq. 6 for the chunk are then
+// one dense product, out[pixel][ch] += W[pixel][entry] F[entry][ch]
+// (32 x NCP x up to 32), taken on the tensor cores (warp-level TF32 MMA in
+// three passes, about FP32 accurate).  A warp stops as soon as all its
+// pixels have stopped, without waiting for the rest of the tile: there is no
+// block-wide barrier.
 #include "kernels.h"
 
 namespace rogs {
 
 int padded_channels(int C) {
-    const int n = 3 + C + 1;
+    const int n = 3 + C + 1;   // a multiple of 8: the MMA n-tile
     if (n <= 8) return 8;
-    if (n <= 12) return 12;
     if (n <= 16) return 16;
     if (n <= 24) return 24;
     if (n <= 32) return 32;
     return 64;
 }
 
-// Features of surfel s (rgb, C logits, depth) into a shared-memory row of NCP floats.
+// Row strides (floats) of the per-warp tables, chosen so that the MMA
+// fragment loads hit 32 different banks: rows 8t apart for t = 0..3.
 template <int NCP>
-__device__ __forceinline__ void stage_features(float* f, uint32_t s, float depth, const SurfelPtrs& sp, int C) {
-    f[0] = sp.rgb[3ull * s];
-    f[1] = sp.rgb[3ull * s + 1];
-    f[2] = sp.rgb[3ull * s + 2];
-    const float* sem = sp.sem + (unsigned long long)C * s;
-    for (int ch = 0; ch < C; ++ch) f[3 + ch] = sem[ch];
-    f[3 + C] = depth;
-#pragma unroll
-    for (int ch = 0; ch < NCP; ++ch)
-        if (ch > 3 + C) f[ch] = 0.0f;
-}
+__host__ __device__ constexpr int feat_stride() { return (NCP % 32 == 8 || NCP % 32 == 24) ? NCP : NCP + 8; }
+constexpr int kWStride = 40;   // weight table: row = entry, column = pixel
 
 template <int NCP>
-__host__ __device__ constexpr int fwd_warp_floats() { return 32 * 4 + 32 * 4 + 32 * NCP + 32; }
+__host__ __device__ constexpr int fwd_warp_floats() {
+    return 32 * 4 + 32 * 4 + 32 * feat_stride<NCP>() + 32 + 32 * kWStride;
+}
 
 template <int TW, int TH, int NCP>
 __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __restrict__ views, int n_views, Consts k,
@@ -56,13 +54,17 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                                                            uint32_t* __restrict__ pix_last,
                                                            StateHeader* __restrict__ hdr) {
     constexpr int WX = TW / 8;
+    constexpr int SF = feat_stride<NCP>();
+    constexpr int NT = NCP / 8;   // MMA n-tiles over the channels
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;   // MMA fragment coordinates
     extern __shared__ float4 smem_fwd[];
     float* wbase = reinterpret_cast<float*>(smem_fwd) + warp * fwd_warp_floats<NCP>();
     float4* s_m = reinterpret_cast<float4*>(wbase);
     float4* s_c = s_m + 32;
     float* s_f = reinterpret_cast<float*>(s_c + 32);
-    uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_f + 32 * NCP);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_f + 32 * SF);
+    float* s_w = reinterpret_cast<float*>(s_idx + 32);
 
     const long long tile = tile_order[blockIdx.x];
     const int vi = view_of_tile(views, n_views, tile);
@@ -81,9 +83,13 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
     const unsigned lt_mask = lanemask_lt();
 
     float T = 1.0f;
-    float acc[NCP];
+    float acc[2][NT][4];   // C fragments: pixels 16 mt + g (+8), channels 8 nt + 2t (+1)
 #pragma unroll
-    for (int ch = 0; ch < NCP; ++ch) acc[ch] = 0.0f;
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.0f;
     uint32_t last = 0, ncomp = 0;
     bool done = !inside;
 
@@ -102,74 +108,108 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
         }
         const unsigned mask = __ballot_sync(kFull, hit);
         if (!mask) continue;
+        const int h = __popc(mask);
+        const int h8 = (h + 7) & ~7;   // k extent of the product, padded with zero rows
         if (hit) {
             const int slot = __popc(mask & lt_mask);
             s_m[slot] = m;
             s_c[slot] = c;
             s_idx[slot] = j - start + 1;
             const float4 d = reinterpret_cast<const float4*>(recs + rec)[2];
-            stage_features<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
+            stage_surfel_features<NCP>(s_f + slot * SF, __float_as_uint(d.z), d.x, sp, C);
+        }
+        if (lane >= h && lane < h8) {   // zero feature rows pad k up to a multiple of 8
+#pragma unroll
+            for (int ch = 0; ch < NCP; ++ch) s_f[lane * SF + ch] = 0.0f;
         }
         __syncwarp();
-        const int h = __popc(mask);
-        if (!done) {
-            // Entries below alpha_min add w = 0 (acc + 0 * f == acc exactly), so
-            // the only branch left is the transmittance stop.
+        // scalar recursion, lane = pixel: entries below alpha_min and entries
+        // after the stop get w = 0
+        int lslot = -1;   // last slot this pixel composited in the chunk
 #pragma unroll 2
-            for (int jj = 0; jj < h; ++jj) {
-                const float4 mm = s_m[jj];
-                const float4 cc = s_c[jj];
-                const float dx = pix_offset(pxc, mm.x, mm.z);
-                const float dy = pix_offset(pyc, mm.y, mm.w);
-                float g;
-                const float a = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
-                const bool valid = a >= amin;
-                const float Tn = __fmul_rn(T, __fsub_rn(1.0f, a));
-                if (valid && Tn < tmin) {
-                    done = true;
-                    break;
-                }
-                const float w = valid ? __fmul_rn(a, T) : 0.0f;
-                const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
+        for (int jj = 0; jj < h; ++jj) {
+            const float4 mm = s_m[jj];
+            const float4 cc = s_c[jj];
+            const float dx = pix_offset(pxc, mm.x, mm.z);
+            const float dy = pix_offset(pyc, mm.y, mm.w);
+            float gp;
+            const float a = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, gp);
+            bool valid = !done && a >= amin;
+            const float Tn = __fmul_rn(T, __fsub_rn(1.0f, a));
+            const bool stop = valid && Tn < tmin;
+            done = done || stop;
+            valid = valid && !stop;
+            s_w[jj * kWStride + lane] = valid ? __fmul_rn(a, T) : 0.0f;
+            T = valid ? Tn : T;
+            lslot = valid ? jj : lslot;
+            ncomp += valid ? 1u : 0u;
+        }
+        if (lslot >= 0) last = s_idx[lslot];
+        for (int jj = h; jj < h8; ++jj) s_w[jj * kWStride + lane] = 0.0f;
+        __syncwarp();
+        // out[pixel][ch] += W[pixel][entry] F[entry][ch] over this chunk's entries
+        for (int k0 = 0; k0 < h8; k0 += 8) {
+            uint32_t ah[2][4], al[2][4];
 #pragma unroll
-                for (int q = 0; q < NCP / 4; ++q) {
-                    const float4 f = f4[q];
-                    acc[4 * q + 0] = fmaf(w, f.x, acc[4 * q + 0]);
-                    acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
-                }
-                T = valid ? Tn : T;
-                last = valid ? s_idx[jj] : last;
-                ncomp += valid ? 1u : 0u;
+            for (int mt = 0; mt < 2; ++mt) {
+                const float* w0 = s_w + (k0 + t) * kWStride + 16 * mt + g;
+                const float* w1 = s_w + (k0 + t + 4) * kWStride + 16 * mt + g;
+                split_tf32(w0[0], ah[mt][0], al[mt][0]);
+                split_tf32(w0[8], ah[mt][1], al[mt][1]);
+                split_tf32(w1[0], ah[mt][2], al[mt][2]);
+                split_tf32(w1[8], ah[mt][3], al[mt][3]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                uint32_t bh[2], bl[2];
+                split_tf32(s_f[(k0 + t) * SF + 8 * nt + g], bh[0], bl[0]);
+                split_tf32(s_f[(k0 + t + 4) * SF + 8 * nt + g], bh[1], bl[1]);
+                mma_tf32x3(acc[0][nt], ah[0], al[0], bh, bl);
+                mma_tf32x3(acc[1][nt], ah[1], al[1], bh, bl);
             }
         }
         __syncwarp();
     }
 
+    const long long plane = (long long)W * H;
+    const int nch = 3 + C + 1;
+    const float ea = expf(exposure_ab[2 * v.exp_idx]);
+    const float eb = exposure_ab[2 * v.exp_idx + 1];
+    float* o = out + (long long)nch * v.pix_base;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int hr = 0; hr < 2; ++hr) {
+            const int p = 16 * mt + g + 8 * hr;   // this fragment row's pixel
+            const int qx = bx + (p & 7), qy = by + (p >> 3);
+            if (qx >= W || qy >= H) continue;
+            float* op = o + (long long)qy * W + qx;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int ch = 8 * nt + 2 * t + cc;
+                    const float val = acc[mt][nt][2 * hr + cc];
+                    if (ch < 3) op[ch * plane] = fmaf(ea, val, eb);
+                    else if (ch < nch) op[ch * plane] = val;
+                }
+        }
     if (inside) {
         const long long pix = v.pix_base + (long long)py * W + px;
-        const long long plane = (long long)W * H;
-        const int nch = 3 + C + 1;
-        float* o = out + (long long)nch * v.pix_base + (long long)py * W + px;
-        const float ea = expf(exposure_ab[2 * v.exp_idx]);
-        const float eb = exposure_ab[2 * v.exp_idx + 1];
-#pragma unroll
-        for (int ch = 0; ch < NCP; ++ch) {
-            if (ch < 3) o[ch * plane] = fmaf(ea, acc[ch], eb);
-            else if (ch < nch) o[ch * plane] = acc[ch];
-        }
         pix_T[pix] = T;
         pix_last[pix] = last;
     }
     // composited-pair counter (E_alg)
     unsigned long long cnt = ncomp;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    for (int o2 = 16; o2 > 0; o2 >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o2);
     if (lane == 0 && cnt) atomicAdd(&hdr->composited, cnt);
 }
 
-static size_t fwd_smem_bytes(int blk, int ncp) { return (size_t)(blk / 32) * 4 * (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32); }
+static size_t fwd_smem_bytes(int blk, int ncp) {
+    const int sf = (ncp % 32 == 8 || ncp % 32 == 24) ? ncp : ncp + 8;
+    return (size_t)(blk / 32) * 4 * (size_t)(32 * 4 + 32 * 4 + 32 * sf + 32 + 32 * kWStride);
+}
 
 template <int TW, int TH, int NCP>
 static void fwd_attr() {
@@ -185,7 +225,7 @@ static void fwd_attr() {
 
 template <int TW, int TH>
 static void prepare_fwd_tile() {
-    fwd_attr<TW, TH, 8>(); fwd_attr<TW, TH, 12>(); fwd_attr<TW, TH, 16>();
+    fwd_attr<TW, TH, 8>(); fwd_attr<TW, TH, 16>();
     fwd_attr<TW, TH, 24>(); fwd_attr<TW, TH, 32>(); fwd_attr<TW, TH, 64>();
 }
 
@@ -210,7 +250,6 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
     } while (0)
     switch (ncp) {
         case 8: ROGS_FWD(8); break;
-        case 12: ROGS_FWD(12); break;
         case 16: ROGS_FWD(16); break;
         case 24: ROGS_FWD(24); break;
         case 32: ROGS_FWD(32); break;

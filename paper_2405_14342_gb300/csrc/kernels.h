@@ -18,6 +18,27 @@ struct SurfelPtrs {
     long long n;
 };
 
+// Features of surfel s -- rgb, the C semantic logits, then the record's depth,
+// zero-padded to NCP -- into a 16-byte aligned shared-memory row.  All loads
+// are issued before the first store (unrolled, predicated on C).
+template <int NCP>
+__device__ __forceinline__ void stage_surfel_features(float* f, uint32_t s, float depth, const SurfelPtrs& sp, int C) {
+    const float* rgb = sp.rgb + 3ull * s;
+    const float* sem = sp.sem + (unsigned long long)C * s;
+    float v[NCP];
+#pragma unroll
+    for (int ch = 0; ch < NCP; ++ch) {
+        float x = 0.0f;
+        if (ch < 3) x = rgb[ch];
+        else if (ch - 3 < C) x = sem[ch - 3];
+        else if (ch - 3 == C) x = depth;
+        v[ch] = x;
+    }
+#pragma unroll
+    for (int q = 0; q < NCP / 4; ++q)
+        reinterpret_cast<float4*>(f)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
 struct GradPtrs {
     float *xyz, *scale, *quat, *opacity, *rgb, *sem, *exposure;
 };
