@@ -32,11 +32,7 @@ int padded_channels(int C) {
     return 64;
 }
 
-// Row strides (floats) of the per-warp tables, chosen so that the MMA
-// fragment loads hit 32 different banks: rows 8t apart for t = 0..3.
-template <int NCP>
-__host__ __device__ constexpr int feat_stride() { return (NCP % 32 == 8 || NCP % 32 == 24) ? NCP : NCP + 8; }
-constexpr int kWStride = 40;   // weight table: row = entry, column = pixel
+constexpr int kWStride = 40;   // weight table: row = entry, column = pixel (rows 8 banks apart)
 
 template <int NCP>
 __host__ __device__ constexpr int fwd_warp_floats() {

@@ -18,6 +18,12 @@ struct SurfelPtrs {
     long long n;
 };
 
+// Row stride (floats) of the per-warp feature / gradient tables of the
+// compositing kernels, chosen so that the MMA fragment loads (rows t = 0..3
+// apart, columns g = 0..7) hit 32 different banks.
+template <int NCP>
+__host__ __device__ constexpr int feat_stride() { return (NCP % 32 == 8 || NCP % 32 == 24) ? NCP : NCP + 8; }
+
 // Features of surfel s -- rgb, the C semantic logits, then the record's depth,
 // zero-padded to NCP -- into a 16-byte aligned shared-memory row.  All loads
 // are issued before the first store (unrolled, predicated on C).
