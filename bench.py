@@ -39,9 +39,9 @@ SM_COUNT, FP32_LANES = 152, 128   # GB300: 152 SMs x 128 FP32 lanes
 # capture, keyed by the sha256 of the source file it was taken from; a
 # different source hash means the kernel changed since and traffic is null.
 NCU_TRAFFIC = {
-    # ncu --set full, one launch of the scene workload (6 x 960x540, 16x16 tiles); see profiles/
-    "composite_bwd": {"bytes": 417_612_032 + 55_536_128, "sha": "d9836ece075a4108"},
-    "composite_fwd": {"bytes": 53_152_000 + 255_647_488, "sha": "e0fc030246e3acfb"},
+    # ncu --set full, one launch of the scene workload (6 x 960x540); see profiles/
+    "composite_bwd": {"sha": "c23c65241d21b641", "16x16": 275_355_136 + 53_743_360},
+    "composite_fwd": {"sha": "a0bc2631dba2fe86", "16x16": 52_616_960 + 256_148_992},
 }
 
 
@@ -321,8 +321,10 @@ def run_ours(args):
     feat = 4 * (3 + C)
     stage_work = {
         "composite_fwd": (P * (4 * nch + 8) + 4 * K + nr * (48 + feat), E * (2 * nch + 18)),
-        "composite_bwd": (P * (4 * nch + 8) + 4 * K + nr * (48 + feat + 4 * (6 + nch)), E * (8 * nch + 33)),
-        "loss": (P * (4 * (3 + C) + 17 + 4 * nch), P * (8 * C + 12)),
+        # the loss of Eqs. 8-9 is fused into the backward: it reads out and the targets
+        "composite_bwd": (P * (4 * nch + 8 + 17) + 4 * K + nr * (48 + feat + 4 * (6 + nch)),
+                          E * (8 * nch + 33) + P * (8 * C + 12)),
+        "loss": (P * 1, P * 1.0),   # |M|: the mask count
         "project_bwd": (nr * (4 * (6 + nch) + 48 + 40 + 4 * (10 + 3 + C)), nr * 200),
         "cull_project": (st.n * 12 + st.n * 40 + nr * (48 + 8 + 8), st.n * 6 * 12 + nr * 300),
         "depth_sort": (4 * nr * 24, 0.0),
@@ -347,7 +349,8 @@ def run_ours(args):
     src = os.path.join(ROOT, "paper_2405_14342_gb300", "csrc",
                        "backward.cu" if dom in ("composite_bwd", "project_bwd") else "composite.cu")
     tr = NCU_TRAFFIC.get(dom)
-    roof["traffic"] = tr["bytes"] if tr and tr.get("sha") == file_sha(src) else None
+    tile_key = f"{tile[0]}x{tile[1]}"
+    roof["traffic"] = tr.get(tile_key) if tr and tr.get("sha") == file_sha(src) else None
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
