@@ -81,21 +81,21 @@ __device__ __forceinline__ float pixel_grad(const BwdArgs& a, const ViewParams& 
             x[ch] = (ch >= 3 && ch < 3 + C) ? o[ch * plane] : 0.0f;
             if (ch >= 3 && ch < 3 + C) mx = fmaxf(mx, x[ch]);
         }
-        float se = 0.0f;
+        // softmax with one exponential per class: e = exp(x - max), p = e / sum e
+        float se = 0.0f, xl = 0.0f;
 #pragma unroll
         for (int ch = 0; ch < NCP; ++ch)
-            if (ch >= 3 && ch < 3 + C) se += expf(x[ch] - mx);
-        const float lse = mx + logf(se);
-        float xl = 0.0f;
-#pragma unroll
-        for (int ch = 0; ch < NCP; ++ch) {
             if (ch >= 3 && ch < 3 + C) {
-                const bool hit = (ch - 3) == lb;
-                if (hit) xl = x[ch];
-                G[ch] = a.lambda_s * inv * (expf(x[ch] - lse) - (hit ? 1.0f : 0.0f));
+                if ((ch - 3) == lb) xl = x[ch];
+                x[ch] = __expf(x[ch] - mx);
+                se += x[ch];
             }
-        }
-        ce = lse - xl;
+        const float rse = 1.0f / se;
+        const float ls = a.lambda_s * inv;
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch)
+            if (ch >= 3 && ch < 3 + C) G[ch] = ls * (x[ch] * rse - ((ch - 3) == lb ? 1.0f : 0.0f));
+        ce = mx + logf(se) - xl;
     }
     return a.lambda_c * l1 + a.lambda_s * ce;
 }

@@ -76,15 +76,17 @@ __global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restr
             float ce = 0.0f;
             const int lb = C > 0 ? label[p] : -1;
             if (lb >= 0 && lb < C) {  // labels outside [0, C) carry no semantic term
+                // softmax with one exponential per class: e = exp(x - max), p = e / sum e
                 float mx = o[3 * plane];
                 for (int ch = 1; ch < C; ++ch) mx = fmaxf(mx, o[(3 + ch) * plane]);
                 float se = 0.0f;
-                for (int ch = 0; ch < C; ++ch) se += expf(o[(3 + ch) * plane] - mx);
-                const float lse = mx + logf(se);
-                ce = lse - o[(3 + lb) * plane];
+                for (int ch = 0; ch < C; ++ch) se += __expf(o[(3 + ch) * plane] - mx);
+                ce = mx + logf(se) - o[(3 + lb) * plane];
+                const float rse = 1.0f / se;
+                const float ls = lambda_s * inv;
                 for (int ch = 0; ch < C; ++ch) {
-                    const float sm = expf(o[(3 + ch) * plane] - lse);
-                    g[(3 + ch) * plane] = lambda_s * inv * (sm - (ch == lb ? 1.0f : 0.0f));
+                    const float e = __expf(o[(3 + ch) * plane] - mx);
+                    g[(3 + ch) * plane] = ls * (e * rse - (ch == lb ? 1.0f : 0.0f));
                 }
             } else {
                 for (int ch = 0; ch < C; ++ch) g[(3 + ch) * plane] = 0.0f;
