@@ -122,9 +122,13 @@ typedef struct {
      pix_last    uint32 per pixel: entries of its tile list up to and including
                  the last composited one
      tile_order  uint32 per tile: tiles by descending list length (the order in
-                 which the compositing kernels are scheduled) */
+                 which the compositing kernels are scheduled)
+     rec_feat    float[NCP] per record, 16-byte aligned rows: the surfel's rgb,
+                 its C logits, the record's depth, then zeros; NCP = 3 + C + 1
+                 rounded up to 8, 16, 24, 32 or 64 (what the compositing
+                 kernels stage per list entry, one aligned row per record) */
 typedef struct {
-    uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, tile_order, total_bytes;
+    uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, tile_order, rec_feat, total_bytes;
     int64_t total_tiles, total_pixels;
 } rogs_state_layout;
 

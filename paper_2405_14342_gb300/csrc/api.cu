@@ -233,6 +233,7 @@ rogs_state_layout layout_for(const rogs_config& cfg, long long total_tiles, long
     L.pix_T = off; off = align256(off + 4 * (size_t)total_pix);
     L.pix_last = off; off = align256(off + 4 * (size_t)total_pix);
     L.tile_order = off; off = align256(off + 4 * (size_t)total_tiles);
+    L.rec_feat = off; off = align256(off + 4 * (size_t)padded_channels(cfg.num_classes) * (size_t)cfg.record_capacity);
     L.total_bytes = off;
     L.total_tiles = total_tiles;
     L.total_pixels = total_pix;
@@ -501,7 +502,8 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     if (n > 0) {
         cull_views(views, n_views, k, sp, ctx->bits, n_words, s);
         scan_visible(ctx->bits, n_words * n_views, ctx->word_off, ctx->bits_tiles, hdr, rcap, s);
-        project_records(views, n_views, k, sp, ctx->bits, ctx->word_off, n_words, recs, rects, ctx->dk_a, ctx->dv_a,
+        project_records(views, n_views, k, sp, ctx->bits, ctx->word_off, n_words, recs, rects,
+                        (float*)(sb + L.rec_feat), ctx->dk_a, ctx->dv_a,
                         rcap, s);
         // depth sort: stable on the binary32 depth key; ties keep (view, surfel) order
         prof_mark(ctx, 1, s);
@@ -521,7 +523,8 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     order_tiles(ranges, total_tiles, tile_order, (unsigned long long)total_tiles <= pcap, ctx->pk_a, ctx->pv_a,
                 ctx->pk_c, ctx->pv_c, ctx->pk_b, ctx->hist, s, cfg.sort_tile);
     prof_mark(ctx, 4, s);
-    composite_fwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs, pair_rec, ranges,
+    composite_fwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs,
+                  (const float*)(sb + L.rec_feat), pair_rec, ranges,
                   tile_order, exposure_ab, out, pix_T, pix_last, hdr, s);
     prof_mark(ctx, -1, s);
     ROGS_CUDA(ctx, cudaGetLastError());
@@ -590,6 +593,7 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
     BwdArgs a{};
     a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs; a.pair_rec = pair_rec; a.ranges = ranges;
+    a.feat = (const float*)(sb + L.rec_feat);
     a.tile_order = tile_order; a.exposure_ab = exposure_ab; a.pix_T = pix_T; a.pix_last = pix_last;
     a.grad_out = grad_out;
     a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
@@ -635,6 +639,7 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     mask_count(mask, total_pix, ctx->loss_counter, s);
     BwdArgs a{};
     a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs;
+    a.feat = (const float*)(sb + L.rec_feat);
     a.pair_rec = (const uint32_t*)(sb + L.pair_rec);
     a.ranges = (const uint2*)(sb + L.tile_range);
     a.tile_order = (const uint32_t*)(sb + L.tile_order);

@@ -188,8 +188,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             s_m[slot] = m;
             s_c[slot] = c;
             s_rec[slot] = rec;
-            const float4 d = reinterpret_cast<const float4*>(a.recs + rec)[2];
-            stage_surfel_features<NCP>(s_f + slot * NCP, __float_as_uint(d.z), d.x, sp, C);
+            stage_record_features<NCP>(s_f + slot * NCP, a.feat, rec);
         }
         __syncwarp();
         // phase A (lane = pixel): reverse recursion over the compacted entries.

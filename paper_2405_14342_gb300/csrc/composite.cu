@@ -42,6 +42,7 @@ __host__ __device__ constexpr int fwd_warp_floats() {
 template <int TW, int TH, int NCP>
 __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __restrict__ views, int n_views, Consts k,
                                                            SurfelPtrs sp, const Record* __restrict__ recs,
+                                                           const float* __restrict__ feat,
                                                            const uint32_t* __restrict__ pair_rec,
                                                            const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ tile_order,
@@ -111,8 +112,7 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
             s_m[slot] = m;
             s_c[slot] = c;
             s_idx[slot] = j - start + 1;
-            const float4 d = reinterpret_cast<const float4*>(recs + rec)[2];
-            stage_surfel_features<NCP>(s_f + slot * SF, __float_as_uint(d.z), d.x, sp, C);
+            stage_record_features<NCP>(s_f + slot * SF, feat, rec);
         }
         if (lane >= h && lane < h8) {   // zero feature rows pad k up to a multiple of 8
 #pragma unroll
@@ -233,7 +233,8 @@ void prepare_composite_fwd() {
 
 template <int TW, int TH>
 static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
-                            Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
+                            Consts k, SurfelPtrs sp, const Record* recs, const float* feat, const uint32_t* pair_rec,
+                            const uint2* ranges,
                             const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T,
                             uint32_t* pix_last, StateHeader* hdr) {
     dim3 grid((unsigned)total_tiles);
@@ -241,7 +242,7 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
     do {                                                                                                       \
         fwd_attr<TW, TH, NCP>();                                                                               \
         composite_fwd_k<TW, TH, NCP><<<grid, TW * TH, fwd_smem_bytes(TW * TH, NCP), s>>>(                     \
-            views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, out, pix_T, pix_last, hdr); \
+            views, n_views, k, sp, recs, feat, pair_rec, ranges, tile_order, exposure_ab, out, pix_T, pix_last, hdr); \
         note_launches(1);                                                                                      \
     } while (0)
     switch (ncp) {
@@ -255,18 +256,18 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
 }
 
 void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
-                   Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
+                   Consts k, SurfelPtrs sp, const Record* recs, const float* feat, const uint32_t* pair_rec, const uint2* ranges,
                    const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
                    cudaStream_t s) {
     const int ncp = padded_channels(C);
     if (tile_w == 32 && tile_h == 8)
-        launch_fwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, out,
+        launch_fwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_rec, ranges, tile_order, exposure_ab, out,
                                pix_T, pix_last, hdr);
     else if (tile_w == 8 && tile_h == 8)
-        launch_fwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, out,
+        launch_fwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_rec, ranges, tile_order, exposure_ab, out,
                               pix_T, pix_last, hdr);
     else
-        launch_fwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, pair_rec, ranges, tile_order, exposure_ab, out,
+        launch_fwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_rec, ranges, tile_order, exposure_ab, out,
                                 pix_T, pix_last, hdr);
 }
 

@@ -24,25 +24,16 @@ struct SurfelPtrs {
 template <int NCP>
 __host__ __device__ constexpr int feat_stride() { return (NCP % 32 == 8 || NCP % 32 == 24) ? NCP : NCP + 8; }
 
-// Features of surfel s -- rgb, the C semantic logits, then the record's depth,
-// zero-padded to NCP -- into a 16-byte aligned shared-memory row.  All loads
-// are issued before the first store (unrolled, predicated on C).
+// Copy of a record's feature row (rgb, C logits, depth, zeros: NCP floats,
+// 16-byte aligned) into a shared-memory row; all loads before the stores.
 template <int NCP>
-__device__ __forceinline__ void stage_surfel_features(float* f, uint32_t s, float depth, const SurfelPtrs& sp, int C) {
-    const float* rgb = sp.rgb + 3ull * s;
-    const float* sem = sp.sem + (unsigned long long)C * s;
-    float v[NCP];
+__device__ __forceinline__ void stage_record_features(float* f, const float* __restrict__ feat, uint32_t rec) {
+    const float4* src = reinterpret_cast<const float4*>(feat + (unsigned long long)rec * NCP);
+    float4 v[NCP / 4];
 #pragma unroll
-    for (int ch = 0; ch < NCP; ++ch) {
-        float x = 0.0f;
-        if (ch < 3) x = rgb[ch];
-        else if (ch - 3 < C) x = sem[ch - 3];
-        else if (ch - 3 == C) x = depth;
-        v[ch] = x;
-    }
+    for (int q = 0; q < NCP / 4; ++q) v[q] = src[q];
 #pragma unroll
-    for (int q = 0; q < NCP / 4; ++q)
-        reinterpret_cast<float4*>(f)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int q = 0; q < NCP / 4; ++q) reinterpret_cast<float4*>(f)[q] = v[q];
 }
 
 struct GradPtrs {
@@ -66,9 +57,11 @@ void scan_visible(const uint32_t* bits, long long n_words_total, uint32_t* word_
                   StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s);
 size_t scan_tile_sums_words(unsigned long long cap);
 // Write records, rects, depth sort keys and values.
+// Writes the records, their tile rectangles, sort keys / values and the
+// per-record feature rows (padded_channels(C) floats each).
 void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, const uint32_t* bits,
-                     const uint32_t* word_off, long long n_words, Record* recs, uint2* rects, uint32_t* keys,
-                     uint32_t* vals, unsigned long long rec_cap, cudaStream_t s);
+                     const uint32_t* word_off, long long n_words, Record* recs, uint2* rects, float* feat,
+                     uint32_t* keys, uint32_t* vals, unsigned long long rec_cap, cudaStream_t s);
 
 // ---- bin.cu
 // Pair offsets per depth-sorted record; total -> hdr->need_pairs, n_pairs clamped.
@@ -90,7 +83,7 @@ void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool s
 int padded_channels(int C);
 void prepare_composite_fwd();   // set the dynamic shared-memory limits (before any capture)
 void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
-                   Consts k, SurfelPtrs sp, const Record* recs, const uint32_t* pair_rec, const uint2* ranges,
+                   Consts k, SurfelPtrs sp, const Record* recs, const float* feat, const uint32_t* pair_rec, const uint2* ranges,
                    const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
                    cudaStream_t s);
 
@@ -104,6 +97,7 @@ struct BwdArgs {
     Consts k;
     SurfelPtrs sp;
     const Record* recs;
+    const float* feat;   // per-record feature rows (padded_channels(C) floats)
     const uint32_t* pair_rec;
     const uint2* ranges;
     const uint32_t* tile_order;

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(kProjThreads) project_k(const ViewParams* __re
                                                            SurfelPtrs sp, const uint32_t* __restrict__ bits,
                                                            const uint32_t* __restrict__ word_off, long long n_words,
                                                            Record* __restrict__ recs, uint2* __restrict__ rects,
+                                                           float* __restrict__ feat, int ncp,
                                                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                            unsigned long long rec_cap) {
     extern __shared__ ViewParams sv[];
@@ -205,6 +206,22 @@ __global__ void __launch_bounds__(kProjThreads) project_k(const ViewParams* __re
             rects[pos] = rc;
             keys[pos] = float_sort_bits(o.key);
             vals[pos] = (uint32_t)pos;
+            // feature row: rgb, the C logits, depth, zeros
+            {
+                const int C = k.C;
+                const float* rgb = sp.rgb + 3ull * (unsigned long long)i;
+                const float* sem = sp.sem + (unsigned long long)C * (unsigned long long)i;
+                float4* fr = reinterpret_cast<float4*>(feat + pos * (unsigned long long)ncp);
+                for (int q = 0; q < ncp / 4; ++q) {
+                    float e[4];
+#pragma unroll
+                    for (int c4 = 0; c4 < 4; ++c4) {
+                        const int ch = 4 * q + c4;
+                        e[c4] = ch < 3 ? rgb[ch] : (ch - 3 < C ? sem[ch - 3] : (ch - 3 == C ? o.depth : 0.0f));
+                    }
+                    fr[q] = make_float4(e[0], e[1], e[2], e[3]);
+                }
+            }
         }
     }
 }
@@ -267,11 +284,12 @@ void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t
 }
 
 void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, const uint32_t* bits,
-                     const uint32_t* word_off, long long n_words, Record* recs, uint2* rects, uint32_t* keys,
-                     uint32_t* vals, unsigned long long rec_cap, cudaStream_t s) {
+                     const uint32_t* word_off, long long n_words, Record* recs, uint2* rects, float* feat,
+                     uint32_t* keys, uint32_t* vals, unsigned long long rec_cap, cudaStream_t s) {
     size_t sm = sizeof(ViewParams) * (size_t)n_views;
     project_k<<<grid_for_words(n_words), kProjThreads, sm, s>>>(views, n_views, k, sp, bits, word_off, n_words, recs,
-                                                                rects, keys, vals, rec_cap);
+                                                                rects, feat, padded_channels(k.C), keys, vals,
+                                                                rec_cap);
     note_launches(1);
 }
 
