@@ -140,6 +140,18 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
 
     float T = 1.0f;
     uint32_t last = 0;
+    if (inside) {
+        const long long pix = v.pix_base + (long long)py * W + px;
+        T = a.pix_T[pix];
+        last = a.pix_last[pix];
+    }
+    const uint32_t wmax = __reduce_max_sync(kFull, last);
+    // the first chunk's list entries are loaded while dL/dout is computed
+    uint32_t rec_first = 0;
+    {
+        const uint32_t j = (wmax > 32u ? wmax - 32u : 0u) + lane;
+        if (j < wmax) rec_first = a.pair_rec[start + j];
+    }
     float G[NCP];
     float lpix = 0.0f;
     float gsum_rgb = 0.0f;
@@ -147,9 +159,6 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         lpix = pixel_grad<NCP>(a, v, px, py, C, G);
         gsum_rgb = G[0] + G[1] + G[2];
         G[0] *= ea; G[1] *= ea; G[2] *= ea;   // through c' = e^a c + b
-        const long long pix = v.pix_base + (long long)py * W + px;
-        T = a.pix_T[pix];
-        last = a.pix_last[pix];
     } else {
 #pragma unroll
         for (int ch = 0; ch < NCP; ++ch) G[ch] = 0.0f;
@@ -160,7 +169,6 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(kFull, l, o);
         if (lane == 0) a.loss_partials[blockIdx.x * kBwdWarpsPerBlock + wib] = l;
     }
-    const uint32_t wmax = __reduce_max_sync(kFull, last);
     __syncwarp();
 
     float Ssum = 0.0f;                          // sum_{j>k} w_j (G . f_j)
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
         if (j < cend) {
-            rec = a.pair_rec[start + j];
+            rec = cend == wmax ? rec_first : a.pair_rec[start + j];
             const float4* r4 = reinterpret_cast<const float4*>(a.recs + rec);
             m = r4[0];
             c = r4[1];
