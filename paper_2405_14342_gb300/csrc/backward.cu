@@ -546,15 +546,24 @@ __global__ void __launch_bounds__(256) project_bwd_k(const ViewParams* __restric
             project_bwd_record(views, sp, recs, rec_grad + r * (unsigned long long)GP, dcol, gp, r);
         }
         const int cnt = n - base < 32ull ? (int)(n - base) : 32;
-        for (int j = 0; j < cnt; ++j) {
-            const uint32_t sj = __shfl_sync(kFull, sid, j);
-            float* row = rec_grad + (base + j) * (unsigned long long)GP + 6;
+        // four records per step, their row loads issued together
+        for (int j0 = 0; j0 < cnt; j0 += 4) {
+            uint32_t sj4[4];   // surfel ids of the four records (all lanes shuffle)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sj4[u] = __shfl_sync(kFull, sid, (j0 + u) & 31);
             for (int c = lane; c < nf; c += 32) {
-                const float val = row[c];
-                if (val == 0.0f) continue;
-                row[c] = 0.0f;
-                if (c < 3) { if (gp.rgb) atomicAdd(&gp.rgb[3ull * sj + c], val); }
-                else if (gp.sem) atomicAdd(&gp.sem[(unsigned long long)C * sj + (c - 3)], val);
+                float val[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    val[u] = j0 + u < cnt ? rec_grad[(base + j0 + u) * (unsigned long long)GP + 6 + c] : 0.0f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t sj = sj4[u];
+                    if (val[u] == 0.0f) continue;
+                    rec_grad[(base + j0 + u) * (unsigned long long)GP + 6 + c] = 0.0f;
+                    if (c < 3) { if (gp.rgb) atomicAdd(&gp.rgb[3ull * sj + c], val[u]); }
+                    else if (gp.sem) atomicAdd(&gp.sem[(unsigned long long)C * sj + (c - 3)], val[u]);
+                }
             }
         }
     }
