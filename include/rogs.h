@@ -126,9 +126,13 @@ typedef struct {
      rec_feat    float[NCP] per record, 16-byte aligned rows: the surfel's rgb,
                  its C logits, the record's depth, then zeros; NCP = 3 + C + 1
                  rounded up to 8, 16, 24, 32 or 64 (what the compositing
-                 kernels stage per list entry, one aligned row per record) */
+                 kernels stage per list entry, one aligned row per record)
+     pair_mc     float[8] per pair, in pair_rec order: the first 32 bytes of
+                 its record (mean_int, mean_frac, conic, alpha), so that a
+                 list walk reads them without going through the record id */
 typedef struct {
-    uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, tile_order, rec_feat, total_bytes;
+    uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, tile_order, rec_feat, pair_mc,
+        total_bytes;
     int64_t total_tiles, total_pixels;
 } rogs_state_layout;
 

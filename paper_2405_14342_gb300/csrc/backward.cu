@@ -180,11 +180,10 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         bool hit = false;
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
-        if (j < cend) {
+        if (j < cend) {   // id, mean and conic are independent loads (pair order)
             rec = cend == wmax ? rec_first : a.pair_rec[start + j];
-            const float4* r4 = reinterpret_cast<const float4*>(a.recs + rec);
-            m = r4[0];
-            c = r4[1];
+            m = a.pair_mc[2ull * (start + j)];
+            c = a.pair_mc[2ull * (start + j) + 1];
             hit = entry_hits_block(m, c, amin, (float)bx, (float)by);
         }
         const unsigned mask = __ballot_sync(kFull, hit);

@@ -80,23 +80,28 @@ void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Recor
 }
 
 __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict__ keys,
+                                                     const uint32_t* __restrict__ pair_rec,
+                                                     const Record* __restrict__ recs,
                                                      const StateHeader* __restrict__ hdr, unsigned long long cap,
-                                                     uint2* __restrict__ ranges) {
+                                                     uint2* __restrict__ ranges, float4* __restrict__ pair_mc) {
     const unsigned long long n = scan_len(&hdr->n_pairs, cap);
     for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
          p += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t t = keys[p];
         if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
         if (p + 1 == n || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+        const float4* r4 = reinterpret_cast<const float4*>(recs + pair_rec[p]);
+        pair_mc[2 * p] = r4[0];
+        pair_mc[2 * p + 1] = r4[1];
     }
 }
 
-void tile_ranges(const uint32_t* sorted_tile, const StateHeader* hdr, unsigned long long pair_cap, uint2* ranges,
-                 cudaStream_t s) {
+void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Record* recs, const StateHeader* hdr,
+                 unsigned long long pair_cap, uint2* ranges, float4* pair_mc, cudaStream_t s) {
     unsigned long long blocks = (pair_cap + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    tile_ranges_k<<<(int)blocks, 256, 0, s>>>(sorted_tile, hdr, pair_cap, ranges);
+    tile_ranges_k<<<(int)blocks, 256, 0, s>>>(sorted_tile, pair_rec, recs, hdr, pair_cap, ranges, pair_mc);
     note_launches(1);
 }
 
