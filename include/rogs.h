@@ -129,10 +129,14 @@ typedef struct {
                  kernels stage per list entry, one aligned row per record)
      pair_mc     float[8] per pair, in pair_rec order: the first 32 bytes of
                  its record (mean_int, mean_frac, conic, alpha), so that a
-                 list walk reads them without going through the record id */
+                 list walk reads them without going through the record id
+     pair_blk    uint8 per pair: bit w set iff the record's footprint can
+                 reach the w-th 8x4 pixel block of its tile (blocks row-major
+                 in the tile; the same conservative test the compositing
+                 kernels use) */
 typedef struct {
     uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, tile_order, rec_feat, pair_mc,
-        total_bytes;
+        pair_blk, total_bytes;
     int64_t total_tiles, total_pixels;
 } rogs_state_layout;
 

@@ -235,6 +235,7 @@ rogs_state_layout layout_for(const rogs_config& cfg, long long total_tiles, long
     L.tile_order = off; off = align256(off + 4 * (size_t)total_tiles);
     L.rec_feat = off; off = align256(off + 4 * (size_t)padded_channels(cfg.num_classes) * (size_t)cfg.record_capacity);
     L.pair_mc = off; off = align256(off + 32 * (size_t)cfg.pair_capacity);
+    L.pair_blk = off; off = align256(off + (size_t)cfg.pair_capacity);
     L.total_bytes = off;
     L.total_tiles = total_tiles;
     L.total_pixels = total_pix;
@@ -519,13 +520,16 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
                          bits_for(total_tiles), ctx->hist, s, cfg.sort_tile);
     }
     ROGS_CUDA(ctx, cudaMemsetAsync(ranges, 0, 8 * (size_t)total_tiles, s));
-    if (n > 0) tile_ranges(ctx->pk_b, pair_rec, recs, hdr, pcap, ranges, (float4*)(sb + L.pair_mc), s);
+    if (n > 0)
+        tile_ranges(ctx->pk_b, pair_rec, recs, views, n_views, k, hdr, pcap, ranges, (float4*)(sb + L.pair_mc),
+                    (uint8_t*)(sb + L.pair_blk), s);
     // longest lists first: the compositing kernels take their tiles in this order
     order_tiles(ranges, total_tiles, tile_order, (unsigned long long)total_tiles <= pcap, ctx->pk_a, ctx->pv_a,
                 ctx->pk_c, ctx->pv_c, ctx->pk_b, ctx->hist, s, cfg.sort_tile);
     prof_mark(ctx, 4, s);
     composite_fwd(cfg.tile_w, cfg.tile_h, cfg.num_classes, views, n_views, total_tiles, k, sp, recs,
-                  (const float*)(sb + L.rec_feat), (const float4*)(sb + L.pair_mc), pair_rec, ranges,
+                  (const float*)(sb + L.rec_feat), (const float4*)(sb + L.pair_mc), (const uint8_t*)(sb + L.pair_blk),
+                  pair_rec, ranges,
                   tile_order, exposure_ab, out, pix_T, pix_last, hdr, s);
     prof_mark(ctx, -1, s);
     ROGS_CUDA(ctx, cudaGetLastError());
@@ -596,6 +600,7 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs; a.pair_rec = pair_rec; a.ranges = ranges;
     a.feat = (const float*)(sb + L.rec_feat);
     a.pair_mc = (const float4*)(sb + L.pair_mc);
+    a.pair_blk = (const uint8_t*)(sb + L.pair_blk);
     a.tile_order = tile_order; a.exposure_ab = exposure_ab; a.pix_T = pix_T; a.pix_last = pix_last;
     a.grad_out = grad_out;
     a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
@@ -643,6 +648,7 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs;
     a.feat = (const float*)(sb + L.rec_feat);
     a.pair_mc = (const float4*)(sb + L.pair_mc);
+    a.pair_blk = (const uint8_t*)(sb + L.pair_blk);
     a.pair_rec = (const uint32_t*)(sb + L.pair_rec);
     a.ranges = (const uint2*)(sb + L.tile_range);
     a.tile_order = (const uint32_t*)(sb + L.tile_order);

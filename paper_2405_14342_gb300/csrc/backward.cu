@@ -180,11 +180,13 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         bool hit = false;
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
-        if (j < cend) {   // id, mean and conic are independent loads (pair order)
-            rec = cend == wmax ? rec_first : a.pair_rec[start + j];
-            m = a.pair_mc[2ull * (start + j)];
-            c = a.pair_mc[2ull * (start + j) + 1];
-            hit = entry_hits_block(m, c, amin, (float)bx, (float)by);
+        if (j < cend) {   // the block mask says whether the entry can reach this warp's block
+            hit = (a.pair_blk[start + j] >> warp) & 1u;
+            if (hit) {
+                rec = cend == wmax ? rec_first : a.pair_rec[start + j];
+                m = a.pair_mc[2ull * (start + j)];
+                c = a.pair_mc[2ull * (start + j) + 1];
+            }
         }
         const unsigned mask = __ballot_sync(kFull, hit);
         cend = cbeg;

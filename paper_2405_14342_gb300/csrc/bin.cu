@@ -82,26 +82,43 @@ void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Recor
 __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict__ keys,
                                                      const uint32_t* __restrict__ pair_rec,
                                                      const Record* __restrict__ recs,
+                                                     const ViewParams* __restrict__ views, int n_views, Consts k,
                                                      const StateHeader* __restrict__ hdr, unsigned long long cap,
-                                                     uint2* __restrict__ ranges, float4* __restrict__ pair_mc) {
+                                                     uint2* __restrict__ ranges, float4* __restrict__ pair_mc,
+                                                     uint8_t* __restrict__ pair_blk) {
     const unsigned long long n = scan_len(&hdr->n_pairs, cap);
+    const int wx = k.tile_w / 8, nw = k.tile_w * k.tile_h / 32;   // 8x4 blocks of a tile
     for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
          p += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t t = keys[p];
         if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
         if (p + 1 == n || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
-        const float4* r4 = reinterpret_cast<const float4*>(recs + pair_rec[p]);
-        pair_mc[2 * p] = r4[0];
-        pair_mc[2 * p + 1] = r4[1];
+        const Record& rec = recs[pair_rec[p]];
+        const float4* r4 = reinterpret_cast<const float4*>(&rec);
+        const float4 m = r4[0], c = r4[1];
+        pair_mc[2 * p] = m;
+        pair_mc[2 * p + 1] = c;
+        const ViewParams& v = views[rec.view];   // the tile is in the record's view
+        const long long lt = (long long)t - v.tile_base;
+        const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
+        const float2 r = block_cull_radii(c, k.alpha_min);
+        uint32_t bm = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int bx = tx * k.tile_w + (w % wx) * 8, by = ty * k.tile_h + (w / wx) * 4;
+            if (box_hits_block(m, r, (float)bx, (float)by)) bm |= 1u << w;
+        }
+        pair_blk[p] = (uint8_t)bm;
     }
 }
 
-void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Record* recs, const StateHeader* hdr,
-                 unsigned long long pair_cap, uint2* ranges, float4* pair_mc, cudaStream_t s) {
+void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Record* recs, const ViewParams* views,
+                 int n_views, Consts k, const StateHeader* hdr, unsigned long long pair_cap, uint2* ranges,
+                 float4* pair_mc, uint8_t* pair_blk, cudaStream_t s) {
     unsigned long long blocks = (pair_cap + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    tile_ranges_k<<<(int)blocks, 256, 0, s>>>(sorted_tile, pair_rec, recs, hdr, pair_cap, ranges, pair_mc);
+    tile_ranges_k<<<(int)blocks, 256, 0, s>>>(sorted_tile, pair_rec, recs, views, n_views, k, hdr, pair_cap, ranges,
+                                              pair_mc, pair_blk);
     note_launches(1);
 }
 

@@ -161,15 +161,24 @@ __device__ __forceinline__ float surfel_alpha(float dx, float dy, float A, float
 // rounding never drops a pixel the exact per-pixel test would keep: the fast
 // log, divisions and reciprocal square root used here are within a few ulp,
 // far inside the 0.2 % + 0.01 px margin.
-__device__ __forceinline__ bool entry_hits_block(float4 m, float4 c, float alpha_min, float bx, float by) {
+// Half-widths (rx, ry) of the padded bounding box; negative when the conic is
+// degenerate (then every block is kept).
+__device__ __forceinline__ float2 block_cull_radii(float4 c, float alpha_min) {
     const float det = c.x * c.z - c.y * c.y;
-    if (!(det > 0.0f)) return true;   // degenerate: keep
+    if (!(det > 0.0f)) return make_float2(-1.0f, -1.0f);
     const float kap = __fdividef(fmaxf(2.0f * __logf(__fdividef(c.w, alpha_min)), 0.0f), det);
     const float qx = fmaxf(kap * c.z, 1e-30f), qy = fmaxf(kap * c.x, 1e-30f);
-    const float rx = qx * rsqrtf(qx) * 1.002f + 0.01f;
-    const float ry = qy * rsqrtf(qy) * 1.002f + 0.01f;
+    return make_float2(qx * rsqrtf(qx) * 1.002f + 0.01f, qy * rsqrtf(qy) * 1.002f + 0.01f);
+}
+
+__device__ __forceinline__ bool box_hits_block(float4 m, float2 r, float bx, float by) {
+    if (r.x < 0.0f) return true;
     const float mx = m.x + m.z, my = m.y + m.w;
-    return (mx + rx >= bx + 0.5f) && (mx - rx <= bx + 7.5f) && (my + ry >= by + 0.5f) && (my - ry <= by + 3.5f);
+    return (mx + r.x >= bx + 0.5f) && (mx - r.x <= bx + 7.5f) && (my + r.y >= by + 0.5f) && (my - r.y <= by + 3.5f);
+}
+
+__device__ __forceinline__ bool entry_hits_block(float4 m, float4 c, float alpha_min, float bx, float by) {
+    return box_hits_block(m, block_cull_radii(c, alpha_min), bx, by);
 }
 
 // ------------------------------------------------------------ tensor cores

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                                                            SurfelPtrs sp, const Record* __restrict__ recs,
                                                            const float* __restrict__ feat,
                                                            const float4* __restrict__ pair_mc,
+                                                           const uint8_t* __restrict__ pair_blk,
                                                            const uint32_t* __restrict__ pair_rec,
                                                            const uint2* __restrict__ ranges,
                                                            const uint32_t* __restrict__ tile_order,
@@ -97,11 +98,13 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
         bool hit = false;
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
-        if (j < end) {   // id, mean and conic are independent loads (pair order)
-            rec = pair_rec[j];
-            m = pair_mc[2ull * j];
-            c = pair_mc[2ull * j + 1];
-            hit = entry_hits_block(m, c, amin, (float)bx, (float)by);
+        if (j < end) {   // the block mask says whether the entry can reach this warp's block
+            hit = (pair_blk[j] >> warp) & 1u;
+            if (hit) {
+                rec = pair_rec[j];
+                m = pair_mc[2ull * j];
+                c = pair_mc[2ull * j + 1];
+            }
         }
         const unsigned mask = __ballot_sync(kFull, hit);
         if (!mask) continue;
@@ -234,7 +237,7 @@ void prepare_composite_fwd() {
 template <int TW, int TH>
 static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, const ViewParams* views, int n_views,
                             Consts k, SurfelPtrs sp, const Record* recs, const float* feat, const float4* pair_mc,
-                            const uint32_t* pair_rec, const uint2* ranges,
+                            const uint8_t* pair_blk, const uint32_t* pair_rec, const uint2* ranges,
                             const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T,
                             uint32_t* pix_last, StateHeader* hdr) {
     dim3 grid((unsigned)total_tiles);
@@ -242,8 +245,8 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
     do {                                                                                                       \
         fwd_attr<TW, TH, NCP>();                                                                               \
         composite_fwd_k<TW, TH, NCP><<<grid, TW * TH, fwd_smem_bytes(TW * TH, NCP), s>>>(                     \
-            views, n_views, k, sp, recs, feat, pair_mc, pair_rec, ranges, tile_order, exposure_ab, out, pix_T,  \
-            pix_last, hdr);                                                                                    \
+            views, n_views, k, sp, recs, feat, pair_mc, pair_blk, pair_rec, ranges, tile_order, exposure_ab, out, \
+            pix_T, pix_last, hdr);                                                                             \
         note_launches(1);                                                                                      \
     } while (0)
     switch (ncp) {
@@ -257,18 +260,18 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
 }
 
 void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
-                   Consts k, SurfelPtrs sp, const Record* recs, const float* feat, const float4* pair_mc, const uint32_t* pair_rec, const uint2* ranges,
+                   Consts k, SurfelPtrs sp, const Record* recs, const float* feat, const float4* pair_mc, const uint8_t* pair_blk, const uint32_t* pair_rec, const uint2* ranges,
                    const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
                    cudaStream_t s) {
     const int ncp = padded_channels(C);
     if (tile_w == 32 && tile_h == 8)
-        launch_fwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_mc, pair_rec, ranges, tile_order, exposure_ab, out,
+        launch_fwd_tile<32, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_mc, pair_blk, pair_rec, ranges, tile_order, exposure_ab, out,
                                pix_T, pix_last, hdr);
     else if (tile_w == 8 && tile_h == 8)
-        launch_fwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_mc, pair_rec, ranges, tile_order, exposure_ab, out,
+        launch_fwd_tile<8, 8>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_mc, pair_blk, pair_rec, ranges, tile_order, exposure_ab, out,
                               pix_T, pix_last, hdr);
     else
-        launch_fwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_mc, pair_rec, ranges, tile_order, exposure_ab, out,
+        launch_fwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_mc, pair_blk, pair_rec, ranges, tile_order, exposure_ab, out,
                                 pix_T, pix_last, hdr);
 }
 

@@ -71,10 +71,12 @@ void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeade
 void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Record* recs, const uint2* rects,
                 const unsigned long long* pair_off, const StateHeader* hdr, unsigned long long rec_cap,
                 uint32_t* pair_keys, uint32_t* pair_vals, unsigned long long pair_cap, cudaStream_t s);
-// Tile ranges of the sorted pairs, and each pair's record mean + conic copied
-// into pair order (pair_mc, two float4 per pair).
-void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Record* recs, const StateHeader* hdr,
-                 unsigned long long pair_cap, uint2* ranges, float4* pair_mc, cudaStream_t s);
+// Tile ranges of the sorted pairs; each pair's record mean + conic copied into
+// pair order (pair_mc, two float4 per pair) and its 8x4-block mask (pair_blk,
+// bit w = entry_hits_block for the tile's w-th block).
+void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Record* recs, const ViewParams* views,
+                 int n_views, Consts k, const StateHeader* hdr, unsigned long long pair_cap, uint2* ranges,
+                 float4* pair_mc, uint8_t* pair_blk, cudaStream_t s);
 void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s);
 // Tile order by descending list length (identity when sort_ok is false);
 // uses ka/va/kb/vb/kalt (>= n_tiles uint32 each) and the radix histogram.
@@ -85,7 +87,7 @@ void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool s
 int padded_channels(int C);
 void prepare_composite_fwd();   // set the dynamic shared-memory limits (before any capture)
 void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n_views, long long total_tiles,
-                   Consts k, SurfelPtrs sp, const Record* recs, const float* feat, const float4* pair_mc, const uint32_t* pair_rec, const uint2* ranges,
+                   Consts k, SurfelPtrs sp, const Record* recs, const float* feat, const float4* pair_mc, const uint8_t* pair_blk, const uint32_t* pair_rec, const uint2* ranges,
                    const uint32_t* tile_order, const float* exposure_ab, float* out, float* pix_T, uint32_t* pix_last, StateHeader* hdr,
                    cudaStream_t s);
 
@@ -101,6 +103,7 @@ struct BwdArgs {
     const Record* recs;
     const float* feat;   // per-record feature rows (padded_channels(C) floats)
     const float4* pair_mc;   // per-pair record mean + conic (two float4), in list order
+    const uint8_t* pair_blk;  // per-pair 8x4-block masks, in list order
     const uint32_t* pair_rec;
     const uint2* ranges;
     const uint32_t* tile_order;

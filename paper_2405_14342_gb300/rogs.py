@@ -64,7 +64,7 @@ class rogs_state_layout(C.Structure):
     _fields_ = [("header", C.c_uint64), ("records", C.c_uint64), ("rects", C.c_uint64), ("pair_rec", C.c_uint64),
                 ("tile_range", C.c_uint64), ("pix_T", C.c_uint64), ("pix_last", C.c_uint64),
                 ("views", C.c_uint64), ("tile_order", C.c_uint64), ("rec_feat", C.c_uint64),
-                ("pair_mc", C.c_uint64),
+                ("pair_mc", C.c_uint64), ("pair_blk", C.c_uint64),
                 ("total_bytes", C.c_uint64),
                 ("total_tiles", C.c_int64),
                 ("total_pixels", C.c_int64)]
