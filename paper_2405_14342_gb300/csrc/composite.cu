@@ -92,14 +92,18 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
     uint32_t last = 0, ncomp = 0;
     bool done = !inside;
 
+    // block masks of the next chunk are loaded one chunk ahead
+    uint32_t bm_next = start + lane < end ? pair_blk[start + lane] : 0u;
     for (uint32_t base = start; base < end; base += 32) {
         if (__all_sync(kFull, done)) break;
         const uint32_t j = base + lane;
+        const uint32_t bm = bm_next;
+        bm_next = j + 32 < end ? pair_blk[j + 32] : 0u;
         bool hit = false;
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
         if (j < end) {   // the block mask says whether the entry can reach this warp's block
-            hit = (pair_blk[j] >> warp) & 1u;
+            hit = (bm >> warp) & 1u;
             if (hit) {
                 rec = pair_rec[j];
                 m = pair_mc[2ull * j];
