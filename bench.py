@@ -39,9 +39,9 @@ SM_COUNT, FP32_LANES = 152, 128   # GB300: 152 SMs x 128 FP32 lanes
 # capture, keyed by the sha256 of the source file it was taken from; a
 # different source hash means the kernel changed since and traffic is null.
 NCU_TRAFFIC = {
-    # ncu --set full, one launch of the scene workload (6 x 960x540); see profiles/
-    "composite_bwd": {"sha": "c23c65241d21b641", "16x16": 275_355_136 + 53_743_360},
-    "composite_fwd": {"sha": "a0bc2631dba2fe86", "16x16": 52_616_960 + 256_148_992},
+    # ncu --set full, one launch of the scene workload (6 x 960x540) per tile shape; see profiles/
+    "composite_bwd": {"sha": "b09764b14413c194", "16x16": 295_771_392 + 54_245_376, "8x8": 325_598_208 + 54_620_928},
+    "composite_fwd": {"sha": "e2984185268c3548", "16x16": 74_577_664 + 256_334_848, "8x8": 105_059_328 + 258_623_488},
 }
 
 
