@@ -7,7 +7,8 @@ take their inputs from the seeded generators in
 ``paper_2405_14342_gb300.scenes``, which hold none of the method's arithmetic.
 
 Each wrapper below calls one function of ``rogs_oracle.c``; the equations it
-follows are cited there (RoGs, Sec. 3.1-3.3, Eqs. 2, 4-9, S1-S2).
+follows are cited there (RoGs, Sec. 3.1-3.3, Eqs. 2, 4-9, S1-S2).  The
+elevation smoothness loss is plain numpy in ``oracle/smooth.py``.
 """
 from __future__ import annotations
 
@@ -284,3 +285,6 @@ def set_threads(n: int):
 
 def num_threads() -> int:
     return int(load().orc_num_threads())
+
+
+from .smooth import neighbour_ids, smooth_loss  # noqa: E402,F401

@@ -197,6 +197,29 @@ def strip_map(C=19, seed=0, length=400.0, width=40.0, spacing=0.1):
     return _assemble(x, y, z, gx, gy, rng, C, grid_shape=(ny, nx)), field
 
 
+def grid_index(m: SurfelMap) -> np.ndarray:
+    """Grid -> surfel index map (ny, nx) int32 of a full-grid map (surfel j*nx + i
+    sits at grid vertex (j, i)); -1 marks a vertex without a surfel."""
+    ny, nx = m.grid_shape
+    if ny * nx != m.n:
+        raise ValueError("map is not a full grid")
+    return np.arange(ny * nx, dtype=np.int32).reshape(ny, nx)
+
+
+def with_holes(m: SurfelMap, frac: float = 0.2, seed: int = 7):
+    """Drop a random fraction of a full-grid map's surfels (off-road vertices),
+    keeping the survivors in order; returns the smaller map and its grid index
+    map with -1 at the holes."""
+    rng = np.random.default_rng(seed)
+    gi = grid_index(m)
+    keep = rng.uniform(size=m.n) >= frac
+    new_id = np.full(m.n, -1, np.int64)
+    new_id[keep] = np.arange(int(keep.sum()))
+    m2 = SurfelMap(m.xyz[keep].copy(), m.scale[keep].copy(), m.quat[keep].copy(), m.opacity[keep].copy(),
+                   m.rgb[keep].copy(), m.sem[keep].copy(), (0, 0))
+    return m2, new_id[gi].astype(np.int32)
+
+
 SURROUND_YAWS = (0.0, 55.0, -55.0, 110.0, -110.0, 180.0)
 
 
