@@ -82,10 +82,17 @@ typedef struct {
 
 /* Surfel map (Sec. 3.1, Eq. 3), device pointers, FP32, row-major:
    xyz [n,3], scale [n,2] = (s_x, s_y) (s_z = 0), quat [n,4] = (w,x,y,z)
-   (normalised inside), opacity [n] = alpha, rgb [n,3], sem [n,C] logits. */
+   (normalised inside), opacity [n] = alpha, rgb [n,3], sem [n,C] logits.
+   Optional grid index map of the meshgrid (supplementary "Smooth Loss K
+   Nearest Neighbor Acceleration"): grid_index, device int32
+   [grid_h][grid_w], the surfel at each grid vertex or -1 where the vertex is
+   off the road; NULL (and grid_w = grid_h = 0) when absent.  Only
+   rogs_smooth_loss reads it. */
 typedef struct {
     const float *xyz, *scale, *quat, *opacity, *rgb, *sem;
     int64_t n;
+    const int32_t* grid_index;
+    int32_t grid_w, grid_h;
 } rogs_surfels;
 
 /* Gradient buffers (device, FP32, same shapes as rogs_surfels plus
@@ -239,6 +246,21 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
                             const float* exposure_ab, int32_t n_exposure, float* out, void* state,
                             const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
                             float lambda_s, float* loss, const rogs_grads* grads, rogs_stream stream);
+
+/* Elevation smoothness loss (Sec. 3.3.2, smoothness equation, K = 4;
+   neighbours as in the supplementary "Smooth Loss K Nearest Neighbor
+   Acceleration"):
+     L_smooth = (1/4) sum_i sum_{j in N(i)} (z_i - z_j)^2
+   where N(i) are the surfels at the grid vertices above, below, left and
+   right of surfel i's vertex in surfels->grid_index, and a vertex off the grid
+   or holding -1 stands for i itself.  Writes lambda_smooth * L_smooth to
+   loss[0] (device float) and ADDS lambda_smooth * dL/dz_i to grad_xyz[3i+2]
+   (device [n,3]; NULL skips the gradient).  z_i = surfels->xyz[3i+2]; only
+   xyz and the grid fields are read.  Errors: ROGS_ERR_INVALID when the grid
+   index or loss pointer is NULL or grid_w, grid_h are not positive.  The sum
+   is taken in a fixed order (the result does not depend on timing). */
+rogs_status rogs_smooth_loss(rogs_ctx* ctx, const rogs_surfels* surfels, float lambda_smooth, float* loss,
+                             float* grad_xyz, rogs_stream stream);
 
 /* Stable LSD radix sort of (key, value) pairs of uint32 on key bits
    [0, key_bits) -- the sort used inside rogs_render_fwd, exposed for

@@ -43,6 +43,7 @@ struct rogs_ctx {
     uint32_t* hist = nullptr;
     unsigned long long *pair_off = nullptr, *pair_tiles = nullptr;
     float* rec_grad = nullptr;
+    float* smooth_partials = nullptr;   // one per CTA of the smoothness-loss stencil
     // grown on demand
     uint32_t *bits = nullptr, *word_off = nullptr, *bits_tiles = nullptr;
     size_t bits_cap = 0;  // words
@@ -332,6 +333,7 @@ rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
     ROGS_ALLOC(ctx->pair_off, R + 1);
     ROGS_ALLOC(ctx->pair_tiles, scan_tile_sums_words(R));
     ROGS_ALLOC(ctx->loss_views, (size_t)kMaxViews);
+    ROGS_ALLOC(ctx->smooth_partials, (size_t)smooth_blocks());
 #undef ROGS_ALLOC
     (void)c0;
     if (st != ROGS_OK) {
@@ -351,7 +353,7 @@ void rogs_destroy(rogs_ctx* ctx) {
     void* ptrs[] = {ctx->dk_a, ctx->dv_a, ctx->dk_b, ctx->dv_b, ctx->dk_c, ctx->dv_c, ctx->pk_a, ctx->pv_a,
                     ctx->pk_b, ctx->pk_c, ctx->pv_c, ctx->hist, ctx->pair_off, ctx->pair_tiles, ctx->rec_grad,
                     ctx->bits, ctx->word_off, ctx->bits_tiles, ctx->loss_partials, ctx->loss_counter,
-                    ctx->loss_views, ctx->poses};
+                    ctx->loss_views, ctx->poses, ctx->smooth_partials};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (const ProfEvent& pe : ctx->prof_pending) {
@@ -665,6 +667,19 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     prof_mark(ctx, 7, s);
     project_bwd(views, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp, s);
     prof_mark(ctx, -1, s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+rogs_status rogs_smooth_loss(rogs_ctx* ctx, const rogs_surfels* surfels, float lambda_smooth, float* loss,
+                             float* grad_xyz, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    if (!surfels || !loss || !surfels->xyz) return fail(ctx, ROGS_ERR_INVALID, "null surfels / loss pointer");
+    if (!surfels->grid_index || surfels->grid_w <= 0 || surfels->grid_h <= 0)
+        return fail(ctx, ROGS_ERR_INVALID, "smoothness loss needs the grid index map");
+    cudaStream_t s = (cudaStream_t)stream;
+    smooth_loss(surfels->grid_index, surfels->grid_w, surfels->grid_h, surfels->xyz, lambda_smooth, loss, grad_xyz,
+                ctx->smooth_partials, s);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }

@@ -130,6 +130,11 @@ void composite_bwd(int tile_w, int tile_h, long long total_tiles, const BwdArgs&
 void project_bwd(const ViewParams* views, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
                  unsigned long long rec_cap, float* rec_grad, int C, GradPtrs g, cudaStream_t s);
 
+// ---- smooth.cu
+int smooth_blocks();   // partials written by smooth_loss
+void smooth_loss(const int32_t* grid_index, int grid_w, int grid_h, const float* xyz, float lambda, float* loss,
+                 float* grad_xyz, float* partials, cudaStream_t s);
+
 // ---- loss.cu
 void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, int C, const float* out,
                   const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c, float lambda_s,

@@ -19,18 +19,24 @@ from . import rogs as R
 @dataclasses.dataclass
 class SurfelTensors:
     """Device copy of a surfel map (Sec. 3.1, Eq. 3): xyz [N,3], scale [N,2],
-    quat [N,4], opacity [N], rgb [N,3], sem [N,C] (FP32, contiguous)."""
+    quat [N,4], opacity [N], rgb [N,3], sem [N,C] (FP32, contiguous), and
+    optionally the grid index map [H,W] int32 (surfel per grid vertex, -1 off
+    the road) used by the smoothness loss."""
     xyz: torch.Tensor
     scale: torch.Tensor
     quat: torch.Tensor
     opacity: torch.Tensor
     rgb: torch.Tensor
     sem: torch.Tensor
+    grid_index: torch.Tensor = None
 
     @staticmethod
-    def from_map(m, device="cuda") -> "SurfelTensors":
+    def from_map(m, device="cuda", grid_index=None) -> "SurfelTensors":
         f = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=device).contiguous()
-        return SurfelTensors(f(m.xyz), f(m.scale), f(m.quat), f(m.opacity), f(m.rgb), f(m.sem))
+        gi = None
+        if grid_index is not None:
+            gi = torch.as_tensor(np.ascontiguousarray(grid_index, dtype=np.int32), device=device).contiguous()
+        return SurfelTensors(f(m.xyz), f(m.scale), f(m.quat), f(m.opacity), f(m.rgb), f(m.sem), gi)
 
     @property
     def n(self) -> int:
@@ -40,7 +46,7 @@ class SurfelTensors:
         return (self.xyz, self.scale, self.quat, self.opacity, self.rgb, self.sem)
 
     def c_struct(self) -> R.rogs_surfels:
-        return R.surfels(self.xyz, self.scale, self.quat, self.opacity, self.rgb, self.sem)
+        return R.surfels(self.xyz, self.scale, self.quat, self.opacity, self.rgb, self.sem, self.grid_index)
 
 
 @dataclasses.dataclass
@@ -163,6 +169,13 @@ class Renderer:
                                       frame.state, tgt_rgb, label, mask, lambda_c, lambda_s, loss,
                                       self.grads_struct(grads), stream)
         return Graph(g, keep=(m, frame, exposure, tgt_rgb, label, mask, loss, grads))
+
+    def smooth_loss(self, m: SurfelTensors, lambda_smooth=0.003, loss=None, grad_xyz=None, stream=None):
+        """lambda * L_smooth over the grid index map (rogs_smooth_loss); the
+        gradient is added into grad_xyz[:, 2] when given."""
+        loss = torch.empty(1, device=m.xyz.device) if loss is None else loss
+        R.rogs_smooth_loss(self.ctx, m.c_struct(), lambda_smooth, loss, grad_xyz, stream)
+        return loss
 
     def render_graph(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, stream=None) -> "Graph":
         g = R.rogs_render_graph_create(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,

@@ -46,7 +46,8 @@ class rogs_camera(C.Structure):
 
 class rogs_surfels(C.Structure):
     _fields_ = [("xyz", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("opacity", C.c_void_p),
-                ("rgb", C.c_void_p), ("sem", C.c_void_p), ("n", C.c_int64)]
+                ("rgb", C.c_void_p), ("sem", C.c_void_p), ("n", C.c_int64), ("grid_index", C.c_void_p),
+                ("grid_w", C.c_int32), ("grid_h", C.c_int32)]
 
 
 class rogs_grads(C.Structure):
@@ -124,6 +125,7 @@ def lib():
         L.rogs_train_graph_create.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P,
                                               C.c_int32, P, P, P, P, P, C.c_float, C.c_float, P,
                                               C.POINTER(rogs_grads), P, C.POINTER(P)]
+        L.rogs_smooth_loss.argtypes = [P, C.POINTER(rogs_surfels), C.c_float, P, P, P]
         L.rogs_train_step.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
                                       P, P, P, P, P, C.c_float, C.c_float, P, C.POINTER(rogs_grads), P]
         L.rogs_render_graph_create.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P,
@@ -143,7 +145,7 @@ def lib():
         L.rogs_profile_read.argtypes = [P, C.POINTER(rogs_profile)]
         L.rogs_launch_count.argtypes = []
         L.rogs_launch_count.restype = C.c_uint64
-        for name in ("rogs_train_step", "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
+        for name in ("rogs_train_step", "rogs_smooth_loss", "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
                      "rogs_serve_get_stats", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
                      "rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
                      "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
@@ -187,11 +189,14 @@ def cameras(cams) -> "C.Array":
     return arr
 
 
-def surfels(xyz, scale, quat, opacity, rgb, sem) -> rogs_surfels:
+def surfels(xyz, scale, quat, opacity, rgb, sem, grid_index=None) -> rogs_surfels:
     s = rogs_surfels()
     s.xyz, s.scale, s.quat, s.opacity = xyz.data_ptr(), scale.data_ptr(), quat.data_ptr(), opacity.data_ptr()
     s.rgb, s.sem = rgb.data_ptr(), (sem.data_ptr() if sem is not None and sem.numel() else None)
     s.n = int(xyz.shape[0])
+    if grid_index is not None:
+        s.grid_index = grid_index.data_ptr()
+        s.grid_h, s.grid_w = int(grid_index.shape[0]), int(grid_index.shape[1])
     return s
 
 
@@ -264,6 +269,11 @@ def rogs_render_bwd(ctx, surf: rogs_surfels, cam_arr, n_views, exposure_ab, stat
     _check(ctx, lib().rogs_render_bwd(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
                                       int(exposure_ab.shape[0]), _ptr(state), _ptr(grad_out), C.byref(grads),
                                       _stream(stream)))
+
+
+def rogs_smooth_loss(ctx, surf: rogs_surfels, lambda_smooth, loss, grad_xyz=None, stream=None):
+    _check(ctx, lib().rogs_smooth_loss(ctx, C.byref(surf), float(lambda_smooth), _ptr(loss), _ptr(grad_xyz),
+                                       _stream(stream)))
 
 
 def rogs_sort_pairs(ctx, keys_in, vals_in, key_bits, keys_out, vals_out, stream=None):
