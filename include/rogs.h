@@ -240,12 +240,16 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
    rogs_render_bwd, except that dL/dout is computed inside the backward kernel
    from `out` and the targets instead of being written to and read back from a
    gradient image (same values as rogs_loss followed by rogs_render_bwd, up to
-   FP32 summation order).  Arguments as in those calls; gradients are ADDED
+   FP32 summation order).  With lambda_smooth != 0 the step also takes the
+   elevation smoothness loss of rogs_smooth_loss (needs surfels->grid_index),
+   so loss[0] = lambda_c L_c + lambda_s L_s + lambda_smooth L_smooth (Eq. 12
+   without the LiDAR term).  Arguments as in those calls; gradients are ADDED
    into `grads`; loss: device float[1]. */
 rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
                             const float* exposure_ab, int32_t n_exposure, float* out, void* state,
                             const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
-                            float lambda_s, float* loss, const rogs_grads* grads, rogs_stream stream);
+                            float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
+                            rogs_stream stream);
 
 /* Elevation smoothness loss (Sec. 3.3.2, smoothness equation, K = 4;
    neighbours as in the supplementary "Smooth Loss K Nearest Neighbor
@@ -352,7 +356,7 @@ typedef struct rogs_graph rogs_graph;
 rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
                                     int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
                                     void* state, const float* tgt_rgb, const int32_t* label, const uint8_t* mask,
-                                    float lambda_c, float lambda_s, float* loss, const rogs_grads* grads,
+                                    float lambda_c, float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
                                     rogs_stream stream, rogs_graph** graph);
 
 /* Same, forward only (rogs_render_fwd). */

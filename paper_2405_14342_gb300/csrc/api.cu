@@ -44,6 +44,7 @@ struct rogs_ctx {
     unsigned long long *pair_off = nullptr, *pair_tiles = nullptr;
     float* rec_grad = nullptr;
     float* smooth_partials = nullptr;   // one per CTA of the smoothness-loss stencil
+    float* smooth_val = nullptr;        // lambda_smooth L_smooth of the current training step
     // grown on demand
     uint32_t *bits = nullptr, *word_off = nullptr, *bits_tiles = nullptr;
     size_t bits_cap = 0;  // words
@@ -334,6 +335,7 @@ rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
     ROGS_ALLOC(ctx->pair_tiles, scan_tile_sums_words(R));
     ROGS_ALLOC(ctx->loss_views, (size_t)kMaxViews);
     ROGS_ALLOC(ctx->smooth_partials, (size_t)smooth_blocks());
+    ROGS_ALLOC(ctx->smooth_val, 1);
 #undef ROGS_ALLOC
     (void)c0;
     if (st != ROGS_OK) {
@@ -353,7 +355,7 @@ void rogs_destroy(rogs_ctx* ctx) {
     void* ptrs[] = {ctx->dk_a, ctx->dv_a, ctx->dk_b, ctx->dv_b, ctx->dk_c, ctx->dv_c, ctx->pk_a, ctx->pv_a,
                     ctx->pk_b, ctx->pk_c, ctx->pv_c, ctx->hist, ctx->pair_off, ctx->pair_tiles, ctx->rec_grad,
                     ctx->bits, ctx->word_off, ctx->bits_tiles, ctx->loss_partials, ctx->loss_counter,
-                    ctx->loss_views, ctx->poses, ctx->smooth_partials};
+                    ctx->loss_views, ctx->poses, ctx->smooth_partials, ctx->smooth_val};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (const ProfEvent& pe : ctx->prof_pending) {
@@ -618,11 +620,14 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
 rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
                             const float* exposure_ab, int32_t n_exposure, float* out, void* state,
                             const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
-                            float lambda_s, float* loss, const rogs_grads* grads, rogs_stream stream) {
+                            float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
+                            rogs_stream stream) {
     if (!ctx) return ROGS_ERR_INVALID;
     const rogs_config& cfg = ctx->cfg;
     if (!tgt_rgb || !mask || !loss || !grads || (cfg.num_classes > 0 && !label))
         return fail(ctx, ROGS_ERR_INVALID, "null target/loss/grads pointer");
+    if (lambda_smooth != 0.0f && (!surfels || !surfels->grid_index || surfels->grid_w <= 0 || surfels->grid_h <= 0))
+        return fail(ctx, ROGS_ERR_INVALID, "smoothness loss needs the grid index map");
     if (grads->quat && ((uintptr_t)grads->quat & 15u)) return fail(ctx, ROGS_ERR_INVALID, "grad quat alignment");
     rogs_status st = rogs_render_fwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, stream);
     if (st != ROGS_OK) return st;
@@ -646,6 +651,9 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
     prof_mark(ctx, 5, s);
     mask_count(mask, total_pix, ctx->loss_counter, s);
+    if (lambda_smooth != 0.0f)   // lambda_smooth L_smooth into a scalar the final loss sum adds, dz into the gradient
+        smooth_loss(surfels->grid_index, surfels->grid_w, surfels->grid_h, surfels->xyz, lambda_smooth,
+                    ctx->smooth_val, grads->xyz, ctx->smooth_partials, s);
     BwdArgs a{};
     a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs;
     a.feat = (const float*)(sb + L.rec_feat);
@@ -663,7 +671,8 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
     prof_mark(ctx, 6, s);
     composite_bwd(cfg.tile_w, cfg.tile_h, total_tiles, a, s);
-    loss_final(ctx->loss_partials, n_partials, ctx->loss_counter, loss, s);
+    loss_final(ctx->loss_partials, n_partials, ctx->loss_counter, lambda_smooth != 0.0f ? ctx->smooth_val : nullptr,
+               loss, s);
     prof_mark(ctx, 7, s);
     project_bwd(views, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp, s);
     prof_mark(ctx, -1, s);
@@ -740,7 +749,8 @@ static rogs_status begin_capture(rogs_ctx* ctx, const rogs_surfels* surfels, con
 rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
                                     int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
                                     void* state, const float* tgt_rgb, const int32_t* label, const uint8_t* mask,
-                                    float lambda_c, float lambda_s, float* loss, const rogs_grads* grads,
+                                    float lambda_c, float lambda_s, float lambda_smooth, float* loss,
+                                    const rogs_grads* grads,
                                     rogs_stream stream, rogs_graph** gout) {
     if (!ctx || !gout) return ROGS_ERR_INVALID;
     *gout = nullptr;
@@ -748,7 +758,7 @@ rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, 
     rogs_status st = begin_capture(ctx, surfels, cams, n_views, s, true);
     if (st != ROGS_OK) return st;
     st = rogs_train_step(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, tgt_rgb, label, mask,
-                         lambda_c, lambda_s, loss, grads, stream);
+                         lambda_c, lambda_s, lambda_smooth, loss, grads, stream);
     return finish_capture(ctx, s, st, gout);
 }
 

@@ -142,7 +142,9 @@ void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, 
                   cudaStream_t s);
 int loss_blocks(long long total_pixels);
 void mask_count(const uint8_t* mask, long long total_pixels, unsigned long long* counter, cudaStream_t s);
-void loss_final(const float* partials, int n, const unsigned long long* counter, float* loss, cudaStream_t s);
+// loss[0] = sum(partials) / |M| (+ extra[0] when extra is not NULL)
+void loss_final(const float* partials, int n, const unsigned long long* counter, const float* extra, float* loss,
+                cudaStream_t s);
 
 // ---- init.cu
 void init_from_poses(const float* grid_xy, long long n, const float* poses_dev, long long n_poses, int exact_plane,

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restr
 // a fixed-order tree; the result does not depend on timing.
 __global__ void __launch_bounds__(1024) loss_final_k(const float* __restrict__ partials, int n,
                                                      const unsigned long long* __restrict__ counter,
-                                                     float* __restrict__ loss) {
+                                                     const float* __restrict__ extra, float* __restrict__ loss) {
     __shared__ float sh[32];
     float s = 0.0f;
 #pragma unroll 8
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(1024) loss_final_k(const float* __restrict__ p
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
         if (threadIdx.x == 0) {
             const unsigned long long nm = *counter;
-            loss[0] = nm ? t / (float)nm : 0.0f;
+            loss[0] = (nm ? t / (float)nm : 0.0f) + (extra ? extra[0] : 0.0f);
         }
     }
 }
@@ -142,7 +142,7 @@ void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, 
     mask_count_k<<<gc, kLossThreads, 0, s>>>(mask, total_pixels, counter);
     loss_k<<<nb > 0 ? nb : 1, kLossThreads, 0, s>>>(views, n_views, total_pixels, C, out, tgt_rgb, label, mask,
                                                     lambda_c, lambda_s, counter, grad_out, partials);
-    loss_final_k<<<1, 1024, 0, s>>>(partials, nb, counter, loss);
+    loss_final_k<<<1, 1024, 0, s>>>(partials, nb, counter, nullptr, loss);
     note_launches(3);
     (void)n_blocks_cap;
 }
@@ -156,8 +156,9 @@ void mask_count(const uint8_t* mask, long long total_pixels, unsigned long long*
     note_launches(1);
 }
 
-void loss_final(const float* partials, int n, const unsigned long long* counter, float* loss, cudaStream_t s) {
-    loss_final_k<<<1, 1024, 0, s>>>(partials, n, counter, loss);
+void loss_final(const float* partials, int n, const unsigned long long* counter, const float* extra, float* loss,
+                cudaStream_t s) {
+    loss_final_k<<<1, 1024, 0, s>>>(partials, n, counter, extra, loss);
     note_launches(1);
 }
 

@@ -155,19 +155,22 @@ class Renderer:
         return g
 
     def train_step(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, tgt_rgb, label, mask,
-                   loss: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06, stream=None):
+                   loss: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06, stream=None, lambda_smooth=0.0):
         """Forward, masked L1 + CE loss and backward with the loss fused into the
-        backward kernel (rogs_train_step); gradients are added into `grads`."""
+        backward kernel (rogs_train_step), plus lambda_smooth L_smooth when
+        nonzero; gradients are added into `grads`."""
         R.rogs_train_step(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out, frame.state,
-                          tgt_rgb, label, mask, lambda_c, lambda_s, loss, self.grads_struct(grads), stream)
+                          tgt_rgb, label, mask, lambda_c, lambda_s, loss, self.grads_struct(grads), stream,
+                          lambda_smooth)
 
     def train_graph(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, tgt_rgb, label, mask,
-                    loss: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06, stream=None) -> "Graph":
+                    loss: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06, stream=None,
+                    lambda_smooth=0.0) -> "Graph":
         """Capture rogs_train_step of `frame` into a CUDA graph (all pointers
         fixed; `stream` must be a non-default stream)."""
         g = R.rogs_train_graph_create(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
                                       frame.state, tgt_rgb, label, mask, lambda_c, lambda_s, loss,
-                                      self.grads_struct(grads), stream)
+                                      self.grads_struct(grads), stream, lambda_smooth)
         return Graph(g, keep=(m, frame, exposure, tgt_rgb, label, mask, loss, grads))
 
     def smooth_loss(self, m: SurfelTensors, lambda_smooth=0.003, loss=None, grad_xyz=None, stream=None):

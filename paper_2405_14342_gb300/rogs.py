@@ -123,11 +123,11 @@ def lib():
                                       P, P, C.POINTER(rogs_grads), P]
         L.rogs_sort_pairs.argtypes = [P, P, P, C.c_int64, C.c_int32, P, P, P]
         L.rogs_train_graph_create.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P,
-                                              C.c_int32, P, P, P, P, P, C.c_float, C.c_float, P,
+                                              C.c_int32, P, P, P, P, P, C.c_float, C.c_float, C.c_float, P,
                                               C.POINTER(rogs_grads), P, C.POINTER(P)]
         L.rogs_smooth_loss.argtypes = [P, C.POINTER(rogs_surfels), C.c_float, P, P, P]
         L.rogs_train_step.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
-                                      P, P, P, P, P, C.c_float, C.c_float, P, C.POINTER(rogs_grads), P]
+                                      P, P, P, P, P, C.c_float, C.c_float, C.c_float, P, C.POINTER(rogs_grads), P]
         L.rogs_render_graph_create.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P,
                                                C.c_int32, P, P, P, C.POINTER(P)]
         L.rogs_graph_launch.argtypes = [P, P]
@@ -296,20 +296,22 @@ def rogs_launch_count() -> int:
 
 
 def rogs_train_graph_create(ctx, surf, cam_arr, n_views, exposure_ab, out, state, tgt_rgb, label, mask, lambda_c,
-                            lambda_s, loss, grads: rogs_grads, stream=None):
+                            lambda_s, loss, grads: rogs_grads, stream=None, lambda_smooth=0.0):
     g = C.c_void_p()
     _check(ctx, lib().rogs_train_graph_create(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
                                               int(exposure_ab.shape[0]), _ptr(out), _ptr(state), _ptr(tgt_rgb),
-                                              _ptr(label), _ptr(mask), float(lambda_c), float(lambda_s), _ptr(loss),
+                                              _ptr(label), _ptr(mask), float(lambda_c), float(lambda_s),
+                                              float(lambda_smooth), _ptr(loss),
                                               C.byref(grads), _stream(stream), C.byref(g)))
     return g
 
 
 def rogs_train_step(ctx, surf, cam_arr, n_views, exposure_ab, out, state, tgt_rgb, label, mask, lambda_c, lambda_s,
-                    loss, grads: rogs_grads, stream=None):
+                    loss, grads: rogs_grads, stream=None, lambda_smooth=0.0):
     _check(ctx, lib().rogs_train_step(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
                                       int(exposure_ab.shape[0]), _ptr(out), _ptr(state), _ptr(tgt_rgb), _ptr(label),
-                                      _ptr(mask), float(lambda_c), float(lambda_s), _ptr(loss), C.byref(grads),
+                                      _ptr(mask), float(lambda_c), float(lambda_s), float(lambda_smooth), _ptr(loss),
+                                      C.byref(grads),
                                       _stream(stream)))
 
 

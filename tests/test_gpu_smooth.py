@@ -87,3 +87,36 @@ def test_missing_grid_is_rejected(R):
     with pytest.raises(rogs.RogsError) as ei:
         rr.smooth_loss(st, 1.0)
     assert ei.value.status == rogs.ROGS_ERR_INVALID
+
+
+def test_training_step_adds_the_smoothness_term(R):
+    """rogs_train_step with lambda_smooth: the loss gains lambda L_smooth and
+    only the z column of the position gradient changes, by lambda dL/dz."""
+    m = scenes.tiny_map(C=8)
+    gi = scenes.grid_index(m)
+    cams = [scenes.tiny_camera()]
+    ex = torch.zeros(1, 2, device="cuda")
+    rr = R.Renderer(8, record_capacity=1 << 16, pair_capacity=1 << 20)
+    st = R.SurfelTensors.from_map(m, grid_index=gi)
+    trgb, lab, msk = R.targets_to_device(scenes.random_targets(cams, 8, seed=9))
+    lam = 0.25
+    res = []
+    for ls in (0.0, lam):
+        fr = rr.frame(cams)
+        loss = torch.empty(1, device="cuda")
+        grads = R.zero_grads(st, ex)
+        rr.train_step(st, fr, ex, trgb, lab, msk, loss, grads, lambda_smooth=ls)
+        torch.cuda.synchronize()
+        res.append((loss.item(), {k: v.cpu().numpy() for k, v in grads.items()}))
+    Lr, gr = oracle.smooth_loss(m.xyz[:, 2].astype(np.float64), gi)
+    assert abs((res[1][0] - res[0][0]) - lam * Lr) <= 1e-5 * max(1.0, abs(res[1][0]))
+    # the rendering gradients are atomic sums: equal up to FP32 summation order
+    d = res[1][1]["xyz"].astype(np.float64) - res[0][1]["xyz"]
+    ref = np.abs(res[0][1]["xyz"]).max()
+    assert np.abs(d[:, :2]).max() <= 1e-6 * ref
+    tol = 1e-5 * lam * np.abs(gr).max() + 1e-6 * ref
+    assert np.abs(d[:, 2] - lam * gr).max() <= tol
+    for k in res[0][1]:
+        if k != "xyz":
+            a0, a1 = res[0][1][k].astype(np.float64), res[1][1][k]
+            assert np.abs(a1 - a0).max() <= 1e-6 * max(np.abs(a0).max(), 1e-30), k
