@@ -266,6 +266,35 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
 rogs_status rogs_smooth_loss(rogs_ctx* ctx, const rogs_surfels* surfels, float lambda_smooth, float* loss,
                              float* grad_xyz, rogs_stream stream);
 
+/* One parameter tensor of the optimiser step: its k-th element (k < n) is
+   param[k * stride] with gradient grad[k * stride] (stride 1 for a whole
+   tensor; param = xyz + 2, grad = grad_xyz + 2, stride 3 for the z column
+   only); m and v are its Adam moments, dense device float[n], zero before the
+   first step; lr its learning rate. */
+typedef struct {
+    float* param;
+    float* grad;
+    float* m;
+    float* v;
+    int64_t n;
+    int32_t stride;
+    float lr;
+} rogs_adam_group;
+
+#define ROGS_MAX_ADAM_GROUPS 16
+
+/* One Adam step (Sec. 4.2: Adam with per-tensor learning rates) over up to
+   ROGS_MAX_ADAM_GROUPS groups in a single launch, at step number `step` >= 1
+   (bias correction): per element
+     m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,
+     p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+   With zero_grad != 0 every gradient element is set to 0 after it is read,
+   ready for the next backward (which adds).  Groups must not overlap.
+   Errors: ROGS_ERR_INVALID for n_groups outside [1, ROGS_MAX_ADAM_GROUPS],
+   step < 1, stride < 1, n < 0 or a NULL pointer in a group with n > 0. */
+rogs_status rogs_adam_step(rogs_ctx* ctx, const rogs_adam_group* groups, int32_t n_groups, int32_t step, float beta1,
+                           float beta2, float eps, int32_t zero_grad, rogs_stream stream);
+
 /* Stable LSD radix sort of (key, value) pairs of uint32 on key bits
    [0, key_bits) -- the sort used inside rogs_render_fwd, exposed for
    testing and reuse.  All pointers device; inputs are not modified; n <=

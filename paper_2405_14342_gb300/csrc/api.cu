@@ -693,6 +693,22 @@ rogs_status rogs_smooth_loss(rogs_ctx* ctx, const rogs_surfels* surfels, float l
     return ROGS_OK;
 }
 
+rogs_status rogs_adam_step(rogs_ctx* ctx, const rogs_adam_group* groups, int32_t n_groups, int32_t step, float beta1,
+                           float beta2, float eps, int32_t zero_grad, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    if (!groups || n_groups < 1 || n_groups > ROGS_MAX_ADAM_GROUPS)
+        return fail(ctx, ROGS_ERR_INVALID, "n_groups outside [1, ROGS_MAX_ADAM_GROUPS]");
+    if (step < 1) return fail(ctx, ROGS_ERR_INVALID, "step must be >= 1");
+    for (int i = 0; i < n_groups; ++i) {
+        const rogs_adam_group& g = groups[i];
+        if (g.n < 0 || g.stride < 1) return fail(ctx, ROGS_ERR_INVALID, "group with n < 0 or stride < 1");
+        if (g.n > 0 && (!g.param || !g.grad || !g.m || !g.v)) return fail(ctx, ROGS_ERR_INVALID, "null group pointer");
+    }
+    adam_step(groups, n_groups, step, beta1, beta2, eps, zero_grad != 0, (cudaStream_t)stream);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
 rogs_status rogs_sort_pairs(rogs_ctx* ctx, const uint32_t* keys_in, const uint32_t* vals_in, int64_t n,
                             int32_t key_bits, uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream) {
     if (!ctx) return ROGS_ERR_INVALID;

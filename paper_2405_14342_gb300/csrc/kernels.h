@@ -2,6 +2,7 @@
 // between the C-ABI in api.cu and the kernel translation units).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -129,6 +130,10 @@ int bwd_loss_partials(long long total_tiles, int tile_w, int tile_h);
 void composite_bwd(int tile_w, int tile_h, long long total_tiles, const BwdArgs& a, cudaStream_t s);
 void project_bwd(const ViewParams* views, SurfelPtrs sp, const Record* recs, const StateHeader* hdr,
                  unsigned long long rec_cap, float* rec_grad, int C, GradPtrs g, cudaStream_t s);
+
+// ---- adam.cu
+void adam_step(const rogs_adam_group* groups, int n_groups, int step, float b1, float b2, float eps, bool zero_grad,
+               cudaStream_t s);
 
 // ---- smooth.cu
 int smooth_blocks();   // partials written by smooth_loss

@@ -257,3 +257,45 @@ def render(renderer: Renderer, cams, xyz, scale, quat, opacity, rgb, sem, exposu
     """Differentiable render of `cams`; returns the flat output planes."""
     frame = renderer.frame(cams) if frame is None else frame
     return RenderFunction.apply(renderer, frame, xyz, scale, quat, opacity, rgb, sem, exposure), frame
+
+
+# Sec. 4.2 learning rates (z: proportional to the scene size, see z_lr)
+PAPER_LR = {"opacity": 1e-4, "scale": 1e-4, "quat": 1e-4, "rgb": 0.008, "sem": 0.1, "exposure": 0.001}
+
+
+def z_lr(step, total_steps, scene_size, start=1.6e-4, end=1.6e-6):
+    """z learning rate: scene size x a ratio falling from 1.6e-4 to 1.6e-6
+    (log-linear in the step; the paper gives only the two ends)."""
+    f = min(max(step / max(total_steps, 1), 0.0), 1.0)
+    return scene_size * start * (end / start) ** f
+
+
+class Adam:
+    """Adam state (m, v) for a SurfelTensors + exposure tensor and one fused
+    step over all of them (rogs_adam_step): z only of the positions, then
+    opacity, scale, quat, rgb, sem, exposure with the paper's rates."""
+
+    def __init__(self, renderer, m: SurfelTensors, exposure: torch.Tensor, lr=None):
+        self.r, self.m, self.exposure = renderer, m, exposure
+        self.lr = dict(PAPER_LR if lr is None else lr)
+        self.t = 0
+        sizes = {"z": m.n, "opacity": m.opacity.numel(), "scale": m.scale.numel(), "quat": m.quat.numel(),
+                 "rgb": m.rgb.numel(), "sem": m.sem.numel(), "exposure": exposure.numel()}
+        self.state = {k: (torch.zeros(n, device=m.xyz.device), torch.zeros(n, device=m.xyz.device))
+                      for k, n in sizes.items()}
+
+    def step(self, grads: dict, z_lr_now: float, zero_grad=True, stream=None):
+        self.t += 1
+        m = self.m
+        groups = []
+        mv = self.state
+        groups.append((m.xyz[:, 2], grads["xyz"][:, 2], *mv["z"], m.n, 3, z_lr_now))
+        for k in ("opacity", "scale", "quat", "rgb", "sem"):
+            p = getattr(m, k)
+            if p.numel():
+                groups.append((p, grads[k], *mv[k], p.numel(), 1, self.lr[k]))
+        groups.append((self.exposure, grads["exposure"], *mv["exposure"], self.exposure.numel(), 1,
+                       self.lr["exposure"]))
+        R.rogs_adam_step(self.r.ctx, groups, self.t, zero_grad=zero_grad, stream=stream)
+        if zero_grad:   # x and y are not learnt (Sec. 4.2): their gradient is dropped
+            grads["xyz"][:, :2].zero_()

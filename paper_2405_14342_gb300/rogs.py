@@ -50,6 +50,14 @@ class rogs_surfels(C.Structure):
                 ("grid_w", C.c_int32), ("grid_h", C.c_int32)]
 
 
+class rogs_adam_group(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p),
+                ("n", C.c_int64), ("stride", C.c_int32), ("lr", C.c_float)]
+
+
+ROGS_MAX_ADAM_GROUPS = 16
+
+
 class rogs_grads(C.Structure):
     _fields_ = [("xyz", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("opacity", C.c_void_p),
                 ("rgb", C.c_void_p), ("sem", C.c_void_p), ("exposure", C.c_void_p)]
@@ -126,6 +134,8 @@ def lib():
                                               C.c_int32, P, P, P, P, P, C.c_float, C.c_float, C.c_float, P,
                                               C.POINTER(rogs_grads), P, C.POINTER(P)]
         L.rogs_smooth_loss.argtypes = [P, C.POINTER(rogs_surfels), C.c_float, P, P, P]
+        L.rogs_adam_step.argtypes = [P, C.POINTER(rogs_adam_group), C.c_int32, C.c_int32, C.c_float, C.c_float,
+                                     C.c_float, C.c_int32, P]
         L.rogs_train_step.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
                                       P, P, P, P, P, C.c_float, C.c_float, C.c_float, P, C.POINTER(rogs_grads), P]
         L.rogs_render_graph_create.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P,
@@ -145,7 +155,7 @@ def lib():
         L.rogs_profile_read.argtypes = [P, C.POINTER(rogs_profile)]
         L.rogs_launch_count.argtypes = []
         L.rogs_launch_count.restype = C.c_uint64
-        for name in ("rogs_train_step", "rogs_smooth_loss", "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
+        for name in ("rogs_train_step", "rogs_smooth_loss", "rogs_adam_step", "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
                      "rogs_serve_get_stats", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
                      "rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
                      "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
@@ -274,6 +284,18 @@ def rogs_render_bwd(ctx, surf: rogs_surfels, cam_arr, n_views, exposure_ab, stat
 def rogs_smooth_loss(ctx, surf: rogs_surfels, lambda_smooth, loss, grad_xyz=None, stream=None):
     _check(ctx, lib().rogs_smooth_loss(ctx, C.byref(surf), float(lambda_smooth), _ptr(loss), _ptr(grad_xyz),
                                        _stream(stream)))
+
+
+def rogs_adam_step(ctx, groups, step, beta1=0.9, beta2=0.999, eps=1e-8, zero_grad=True, stream=None):
+    """groups: list of (param, grad, m, v, n, stride, lr) with device tensors
+    (param / grad may be views offset into a larger tensor)."""
+    arr = (rogs_adam_group * len(groups))()
+    for i, (p, g, m, v, n, stride, lr) in enumerate(groups):
+        arr[i].param, arr[i].grad = p.data_ptr(), g.data_ptr()
+        arr[i].m, arr[i].v = m.data_ptr(), v.data_ptr()
+        arr[i].n, arr[i].stride, arr[i].lr = int(n), int(stride), float(lr)
+    _check(ctx, lib().rogs_adam_step(ctx, arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
+                                     1 if zero_grad else 0, _stream(stream)))
 
 
 def rogs_sort_pairs(ctx, keys_in, vals_in, key_bits, keys_out, vals_out, stream=None):
