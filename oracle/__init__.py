@@ -8,8 +8,9 @@ take their inputs from the seeded generators in
 
 Each wrapper below calls one function of ``rogs_oracle.c``; the equations it
 follows are cited there (RoGs, Sec. 3.1-3.3, Eqs. 2, 4-9, S1-S2).  The
-elevation smoothness loss is plain numpy in ``oracle/smooth.py`` and the
-optimiser step in ``oracle/adam.py``.
+elevation smoothness loss is plain numpy in ``oracle/smooth.py``, the
+optimiser step in ``oracle/adam.py`` and the LiDAR elevation loss in
+``oracle/lidar.py``.
 """
 from __future__ import annotations
 
@@ -290,3 +291,4 @@ def num_threads() -> int:
 
 from .smooth import neighbour_ids, smooth_loss  # noqa: E402,F401
 from .adam import adam_step, z_learning_rate  # noqa: E402,F401
+from .lidar import elev_loss, nearest_elevation  # noqa: E402,F401

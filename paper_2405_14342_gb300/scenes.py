@@ -220,6 +220,17 @@ def with_holes(m: SurfelMap, frac: float = 0.2, seed: int = 7):
     return m2, new_id[gi].astype(np.int32)
 
 
+def lidar_points(height, x_range, y_range, n, noise=0.01, seed=5):
+    """Synthetic LiDAR returns on the road: n points uniform in the xy box,
+    z = height(x, y) + N(0, noise); float32 [n, 3].  `height` is any callable
+    returning the surface height (e.g. a RandomField's first output)."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(x_range[0], x_range[1], n)
+    y = rng.uniform(y_range[0], y_range[1], n)
+    z = np.asarray(height(x, y)) + rng.normal(0.0, noise, n)
+    return np.stack([x, y, z], -1).astype(np.float32)
+
+
 SURROUND_YAWS = (0.0, 55.0, -55.0, 110.0, -110.0, 180.0)
 
 
