@@ -266,6 +266,26 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
 rogs_status rogs_smooth_loss(rogs_ctx* ctx, const rogs_surfels* surfels, float lambda_smooth, float* loss,
                              float* grad_xyz, rogs_stream stream);
 
+/* LiDAR elevation targets for L_z (Sec. 3.3.2, LiDAR supervision): for each
+   surfel, zbar_i = z of the point of `points` (device float [n_points, 3],
+   x, y, z) nearest to the surfel centre in the xy-plane, among the points
+   within `radius` of it; NaN when there is none; equal distances go to the
+   lower point index.  Writes z_target (device float [n]).  Meant to run once
+   per point cloud: it may allocate scratch (a spatial hash of the points,
+   held by the context), so it is not for stream capture.  Errors:
+   ROGS_ERR_INVALID for NULL pointers, radius <= 0 or n_points >= 2^31;
+   ROGS_ERR_OOM when the scratch cannot be allocated. */
+rogs_status rogs_elev_targets(rogs_ctx* ctx, const rogs_surfels* surfels, const float* points, int64_t n_points,
+                              float radius, float* z_target, rogs_stream stream);
+
+/* LiDAR elevation loss (Sec. 3.3.2, L_z = sum_i (z_i - zbar_i)^2 over the
+   surfels with a finite target): ADDS lambda_z L_z to loss[0] (device float,
+   so it composes with rogs_train_step's loss) and lambda_z dL/dz_i =
+   2 lambda_z (z_i - zbar_i) to grad_xyz[3i+2] (NULL skips the gradient).
+   The sum is taken in a fixed order. */
+rogs_status rogs_elev_loss(rogs_ctx* ctx, const rogs_surfels* surfels, const float* z_target, float lambda_z,
+                           float* loss, float* grad_xyz, rogs_stream stream);
+
 /* One parameter tensor of the optimiser step: its k-th element (k < n) is
    param[k * stride] with gradient grad[k * stride] (stride 1 for a whole
    tensor; param = xyz + 2, grad = grad_xyz + 2, stride 3 for the z column

@@ -45,6 +45,9 @@ struct rogs_ctx {
     float* rec_grad = nullptr;
     float* smooth_partials = nullptr;   // one per CTA of the smoothness-loss stencil
     float* smooth_val = nullptr;        // lambda_smooth L_smooth of the current training step
+    float* elev_partials = nullptr;     // one per CTA of the LiDAR elevation loss
+    LidarScratch lidar{};               // point-cloud hash of rogs_elev_targets
+    size_t lidar_cap = 0, lidar_hist_cap = 0, lidar_range_cap = 0;
     // grown on demand
     uint32_t *bits = nullptr, *word_off = nullptr, *bits_tiles = nullptr;
     size_t bits_cap = 0;  // words
@@ -336,6 +339,7 @@ rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
     ROGS_ALLOC(ctx->loss_views, (size_t)kMaxViews);
     ROGS_ALLOC(ctx->smooth_partials, (size_t)smooth_blocks());
     ROGS_ALLOC(ctx->smooth_val, 1);
+    ROGS_ALLOC(ctx->elev_partials, (size_t)elev_blocks());
 #undef ROGS_ALLOC
     (void)c0;
     if (st != ROGS_OK) {
@@ -355,7 +359,9 @@ void rogs_destroy(rogs_ctx* ctx) {
     void* ptrs[] = {ctx->dk_a, ctx->dv_a, ctx->dk_b, ctx->dv_b, ctx->dk_c, ctx->dv_c, ctx->pk_a, ctx->pv_a,
                     ctx->pk_b, ctx->pk_c, ctx->pv_c, ctx->hist, ctx->pair_off, ctx->pair_tiles, ctx->rec_grad,
                     ctx->bits, ctx->word_off, ctx->bits_tiles, ctx->loss_partials, ctx->loss_counter,
-                    ctx->loss_views, ctx->poses, ctx->smooth_partials, ctx->smooth_val};
+                    ctx->loss_views, ctx->poses, ctx->smooth_partials, ctx->smooth_val, ctx->elev_partials,
+                    ctx->lidar.keys, ctx->lidar.vals, ctx->lidar.skeys, ctx->lidar.svals, ctx->lidar.kalt,
+                    ctx->lidar.valt, ctx->lidar.hist, ctx->lidar.ranges, ctx->lidar.sorted};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (const ProfEvent& pe : ctx->prof_pending) {
@@ -689,6 +695,56 @@ rogs_status rogs_smooth_loss(rogs_ctx* ctx, const rogs_surfels* surfels, float l
     cudaStream_t s = (cudaStream_t)stream;
     smooth_loss(surfels->grid_index, surfels->grid_w, surfels->grid_h, surfels->xyz, lambda_smooth, loss, grad_xyz,
                 ctx->smooth_partials, s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+rogs_status rogs_elev_targets(rogs_ctx* ctx, const rogs_surfels* surfels, const float* points, int64_t n_points,
+                              float radius, float* z_target, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    if (!surfels || !z_target || (surfels->n > 0 && !surfels->xyz) || n_points < 0 || (n_points > 0 && !points))
+        return fail(ctx, ROGS_ERR_INVALID, "null surfels / points / z_target");
+    if (!(radius > 0.0f) || n_points >= (1ll << 31)) return fail(ctx, ROGS_ERR_INVALID, "radius <= 0 or too many points");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t m = (size_t)(n_points > 0 ? n_points : 1);
+    const size_t nb = (size_t)1 << lidar_bucket_bits(n_points);
+    LidarScratch& w = ctx->lidar;
+    rogs_status st = ROGS_OK;
+    if (m > ctx->lidar_cap) {
+        size_t c[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (st == ROGS_OK) st = grow(ctx, w.keys, c[0], m, s);
+        if (st == ROGS_OK) st = grow(ctx, w.vals, c[1], m, s);
+        if (st == ROGS_OK) st = grow(ctx, w.skeys, c[2], m, s);
+        if (st == ROGS_OK) st = grow(ctx, w.svals, c[3], m, s);
+        if (st == ROGS_OK) st = grow(ctx, w.kalt, c[4], m, s);
+        if (st == ROGS_OK) st = grow(ctx, w.valt, c[5], m, s);
+        if (st == ROGS_OK) st = grow(ctx, w.sorted, c[6], m, s);
+        if (st != ROGS_OK) return st;
+        ctx->lidar_cap = m;
+    }
+    if (radix_hist_words(m) > ctx->lidar_hist_cap) {
+        size_t c = 0;
+        st = grow(ctx, w.hist, c, radix_hist_words(m), s);
+        if (st != ROGS_OK) return st;
+        ctx->lidar_hist_cap = radix_hist_words(m);
+    }
+    if (nb > ctx->lidar_range_cap) {
+        size_t c = 0;
+        st = grow(ctx, w.ranges, c, nb, s);
+        if (st != ROGS_OK) return st;
+        ctx->lidar_range_cap = nb;
+    }
+    lidar_targets(surfels->xyz, surfels->n, points, n_points, radius, w, z_target, s);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+rogs_status rogs_elev_loss(rogs_ctx* ctx, const rogs_surfels* surfels, const float* z_target, float lambda_z,
+                           float* loss, float* grad_xyz, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    if (!surfels || !z_target || !loss || (surfels->n > 0 && !surfels->xyz))
+        return fail(ctx, ROGS_ERR_INVALID, "null surfels / z_target / loss");
+    elev_loss(surfels->xyz, surfels->n, z_target, lambda_z, loss, grad_xyz, ctx->elev_partials, (cudaStream_t)stream);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }

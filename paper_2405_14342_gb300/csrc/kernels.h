@@ -135,6 +135,19 @@ void project_bwd(const ViewParams* views, SurfelPtrs sp, const Record* recs, con
 void adam_step(const rogs_adam_group* groups, int n_groups, int step, float b1, float b2, float eps, bool zero_grad,
                cudaStream_t s);
 
+// ---- lidar.cu
+struct LidarScratch {   // point-cloud hash: capacity m points, 2^lidar_bucket_bits(m) buckets
+    uint32_t *keys, *vals, *skeys, *svals, *kalt, *valt, *hist;
+    uint2* ranges;
+    float4* sorted;
+};
+int lidar_bucket_bits(long long m);
+int elev_blocks();   // partials written by elev_loss
+void lidar_targets(const float* xyz, long long n, const float* pts, long long m, float radius, LidarScratch& w,
+                   float* zbar, cudaStream_t s);
+void elev_loss(const float* xyz, long long n, const float* zbar, float lambda, float* loss, float* grad_xyz,
+               float* partials, cudaStream_t s);
+
 // ---- smooth.cu
 int smooth_blocks();   // partials written by smooth_loss
 void smooth_loss(const int32_t* grid_index, int grid_w, int grid_h, const float* xyz, float lambda, float* loss,

@@ -173,6 +173,17 @@ class Renderer:
                                       self.grads_struct(grads), stream, lambda_smooth)
         return Graph(g, keep=(m, frame, exposure, tgt_rgb, label, mask, loss, grads))
 
+    def elev_targets(self, m: SurfelTensors, points: torch.Tensor, radius=0.1, stream=None) -> torch.Tensor:
+        """LiDAR elevation targets zbar [n] (NaN where no point is within radius)."""
+        zt = torch.empty(m.n, device=m.xyz.device)
+        R.rogs_elev_targets(self.ctx, m.c_struct(), points, radius, zt, stream)
+        return zt
+
+    def elev_loss(self, m: SurfelTensors, z_target, lambda_z, loss, grad_xyz=None, stream=None):
+        """loss[0] += lambda_z L_z; lambda_z dL/dz added into grad_xyz[:, 2]."""
+        R.rogs_elev_loss(self.ctx, m.c_struct(), z_target, lambda_z, loss, grad_xyz, stream)
+        return loss
+
     def smooth_loss(self, m: SurfelTensors, lambda_smooth=0.003, loss=None, grad_xyz=None, stream=None):
         """lambda * L_smooth over the grid index map (rogs_smooth_loss); the
         gradient is added into grad_xyz[:, 2] when given."""

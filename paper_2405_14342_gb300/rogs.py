@@ -134,6 +134,8 @@ def lib():
                                               C.c_int32, P, P, P, P, P, C.c_float, C.c_float, C.c_float, P,
                                               C.POINTER(rogs_grads), P, C.POINTER(P)]
         L.rogs_smooth_loss.argtypes = [P, C.POINTER(rogs_surfels), C.c_float, P, P, P]
+        L.rogs_elev_targets.argtypes = [P, C.POINTER(rogs_surfels), P, C.c_int64, C.c_float, P, P]
+        L.rogs_elev_loss.argtypes = [P, C.POINTER(rogs_surfels), P, C.c_float, P, P, P]
         L.rogs_adam_step.argtypes = [P, C.POINTER(rogs_adam_group), C.c_int32, C.c_int32, C.c_float, C.c_float,
                                      C.c_float, C.c_int32, P]
         L.rogs_train_step.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
@@ -155,7 +157,8 @@ def lib():
         L.rogs_profile_read.argtypes = [P, C.POINTER(rogs_profile)]
         L.rogs_launch_count.argtypes = []
         L.rogs_launch_count.restype = C.c_uint64
-        for name in ("rogs_train_step", "rogs_smooth_loss", "rogs_adam_step", "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
+        for name in ("rogs_train_step", "rogs_smooth_loss", "rogs_adam_step", "rogs_elev_targets", "rogs_elev_loss",
+                     "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
                      "rogs_serve_get_stats", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
                      "rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
                      "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
@@ -284,6 +287,16 @@ def rogs_render_bwd(ctx, surf: rogs_surfels, cam_arr, n_views, exposure_ab, stat
 def rogs_smooth_loss(ctx, surf: rogs_surfels, lambda_smooth, loss, grad_xyz=None, stream=None):
     _check(ctx, lib().rogs_smooth_loss(ctx, C.byref(surf), float(lambda_smooth), _ptr(loss), _ptr(grad_xyz),
                                        _stream(stream)))
+
+
+def rogs_elev_targets(ctx, surf: rogs_surfels, points, radius, z_target, stream=None):
+    _check(ctx, lib().rogs_elev_targets(ctx, C.byref(surf), _ptr(points), int(points.shape[0]), float(radius),
+                                        _ptr(z_target), _stream(stream)))
+
+
+def rogs_elev_loss(ctx, surf: rogs_surfels, z_target, lambda_z, loss, grad_xyz=None, stream=None):
+    _check(ctx, lib().rogs_elev_loss(ctx, C.byref(surf), _ptr(z_target), float(lambda_z), _ptr(loss), _ptr(grad_xyz),
+                                     _stream(stream)))
 
 
 def rogs_adam_step(ctx, groups, step, beta1=0.9, beta2=0.999, eps=1e-8, zero_grad=True, stream=None):
