@@ -253,6 +253,23 @@ def run_ours(args):
     adam_elems = sum(v[0].numel() for v in opt.state.values())
     del opt, st_opt
 
+    # ---- LiDAR supervision (outside the metric): nearest-point targets for the
+    # map from 2M synthetic returns (once per cloud), then L_z per step
+    lidar = None
+    if rank == 0:
+        pts = torch.as_tensor(scenes.lidar_points(lambda x, y: field(x, y)[0], (0.0, 400.0), (0.0, 40.0),
+                                                  2_000_000, seed=6), device="cuda")
+        zt = rr.elev_targets(st, pts, 0.1)
+        torch.cuda.synchronize()
+        ms_targets = _timed(lambda k: rr.elev_targets(st, pts, 0.1), 3, 1, None) / 3
+        lz = torch.zeros(1, device="cuda")
+        gz = torch.zeros_like(st.xyz)
+        ms_lz = _timed(lambda k: rr.elev_loss(st, zt, 0.02, lz, gz), args.steps, 1, None) / args.steps
+        lidar = {"points": int(pts.shape[0]), "radius_m": 0.1,
+                 "with_target": int(torch.isfinite(zt).sum().item()),
+                 "targets_ms": round(ms_targets, 4), "loss_ms": round(ms_lz, 4)}
+        del pts, zt, lz, gz
+
     # per-step counts of the timed steps (deterministic per timestep)
     comp, nrec, npair = 0, 0, 0
     for k in range(args.steps):
@@ -411,6 +428,7 @@ def run_ours(args):
         "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof.items()},
         "counts_per_step": {"records": round(nr), "pairs": round(K), "composited": round(E)},
         "gpu_launches": int(launches),
+        "lidar_supervision": lidar,
         # outside the metric (the paper's optimiser step): bytes = 32 per element (p, g, m, v read; p, m, v, g written)
         "optimizer_step": {"kind": "fused Adam, Sec. 4.2 learning rates", "elements": int(adam_elems),
                            "ms": round(ms_adam, 4),
