@@ -266,6 +266,24 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
 rogs_status rogs_smooth_loss(rogs_ctx* ctx, const rogs_surfels* surfels, float lambda_smooth, float* loss,
                              float* grad_xyz, rogs_stream stream);
 
+/* Chunked BEV export (supplementary "Orthogonal Rendering Acceleration"):
+   a straight-down orthographic render of the map over the ground rectangle
+   x in [x0, x0 + width res], y in [y1 - height res, y1] -- image x along +x,
+   image y along -y from the top edge y1, res metres per pixel, camera at
+   height cam_z -- rendered as a grid of chunk x chunk-pixel orthographic
+   cameras (the paper: 2000 x 2000 at 0.05 m/px; edge chunks are smaller),
+   `batch` chunks per rogs_render_fwd launch, stitched into `image` (device
+   float [3 + C + 1][height][width] planes: rgb after exposure `exposure_idx`,
+   the C logits, depth).  Chunks are batched and stitched on `stream`; the
+   call synchronises once per batch to check the capacities.  Allocates the
+   batch's output and state in the context on first use (not for stream
+   capture).  Errors: ROGS_ERR_INVALID for bad sizes, batch outside [1, 16]
+   or a bad exposure index; ROGS_ERR_CAPACITY when a batch overflows the
+   record or pair capacity (use a smaller batch or larger capacities). */
+rogs_status rogs_bev_export(rogs_ctx* ctx, const rogs_surfels* surfels, const float* exposure_ab, int32_t n_exposure,
+                            int32_t exposure_idx, double x0, double y1, float res, float cam_z, int32_t width,
+                            int32_t height, int32_t chunk, int32_t batch, float* image, rogs_stream stream);
+
 /* LiDAR elevation targets for L_z (Sec. 3.3.2, LiDAR supervision): for each
    surfel, zbar_i = z of the point of `points` (device float [n_points, 3],
    x, y, z) nearest to the surfel centre in the xy-plane, among the points

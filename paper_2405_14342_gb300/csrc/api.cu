@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -47,6 +48,9 @@ struct rogs_ctx {
     float* smooth_val = nullptr;        // lambda_smooth L_smooth of the current training step
     float* elev_partials = nullptr;     // one per CTA of the LiDAR elevation loss
     LidarScratch lidar{};               // point-cloud hash of rogs_elev_targets
+    float* bev_out = nullptr;           // per-batch chunk outputs of rogs_bev_export
+    uint8_t* bev_state = nullptr;
+    size_t bev_out_cap = 0, bev_state_cap = 0;
     size_t lidar_cap = 0, lidar_hist_cap = 0, lidar_range_cap = 0;
     // grown on demand
     uint32_t *bits = nullptr, *word_off = nullptr, *bits_tiles = nullptr;
@@ -361,7 +365,8 @@ void rogs_destroy(rogs_ctx* ctx) {
                     ctx->bits, ctx->word_off, ctx->bits_tiles, ctx->loss_partials, ctx->loss_counter,
                     ctx->loss_views, ctx->poses, ctx->smooth_partials, ctx->smooth_val, ctx->elev_partials,
                     ctx->lidar.keys, ctx->lidar.vals, ctx->lidar.skeys, ctx->lidar.svals, ctx->lidar.kalt,
-                    ctx->lidar.valt, ctx->lidar.hist, ctx->lidar.ranges, ctx->lidar.sorted};
+                    ctx->lidar.valt, ctx->lidar.hist, ctx->lidar.ranges, ctx->lidar.sorted, ctx->bev_out,
+                    ctx->bev_state};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (const ProfEvent& pe : ctx->prof_pending) {
@@ -745,6 +750,78 @@ rogs_status rogs_elev_loss(rogs_ctx* ctx, const rogs_surfels* surfels, const flo
     if (!surfels || !z_target || !loss || (surfels->n > 0 && !surfels->xyz))
         return fail(ctx, ROGS_ERR_INVALID, "null surfels / z_target / loss");
     elev_loss(surfels->xyz, surfels->n, z_target, lambda_z, loss, grad_xyz, ctx->elev_partials, (cudaStream_t)stream);
+    ROGS_CUDA(ctx, cudaGetLastError());
+    return ROGS_OK;
+}
+
+rogs_status rogs_bev_export(rogs_ctx* ctx, const rogs_surfels* surfels, const float* exposure_ab, int32_t n_exposure,
+                            int32_t exposure_idx, double x0, double y1, float res, float cam_z, int32_t width,
+                            int32_t height, int32_t chunk, int32_t batch, float* image, rogs_stream stream) {
+    if (!ctx) return ROGS_ERR_INVALID;
+    if (!surfels || !exposure_ab || !image) return fail(ctx, ROGS_ERR_INVALID, "null surfels / exposure / image");
+    if (width < 1 || height < 1 || chunk < 1 || !(res > 0.0f) || batch < 1 || batch > kMaxStitch || batch > kMaxViews)
+        return fail(ctx, ROGS_ERR_INVALID, "bad export size, chunk, resolution or batch");
+    if (exposure_idx < 0 || exposure_idx >= n_exposure) return fail(ctx, ROGS_ERR_INVALID, "exposure_idx out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nch = 3 + ctx->cfg.num_classes + 1;
+    const int nx = (width + chunk - 1) / chunk, ny = (height + chunk - 1) / chunk;
+    std::vector<rogs_camera> cams;
+    std::vector<int> ox, oy;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const int cw = std::min(chunk, width - i * chunk), chh = std::min(chunk, height - j * chunk);
+            // straight down: image x along +x, image y along -y from the top edge y1
+            const double cxw = x0 + ((double)i * chunk + 0.5 * cw) * res;
+            const double cyw = y1 - ((double)j * chunk + 0.5 * chh) * res;
+            rogs_camera c{};
+            c.kind = ROGS_ORTHO;
+            c.width = cw;
+            c.height = chh;
+            c.exposure_idx = exposure_idx;
+            c.use_box_cull = 0;
+            c.fx = c.fy = (float)(1.0 / res);
+            c.cx = 0.5f * (float)cw;
+            c.cy = 0.5f * (float)chh;
+            const double Rm[9] = {1, 0, 0, 0, -1, 0, 0, 0, -1};
+            const double cen[3] = {cxw, cyw, (double)cam_z};
+            for (int r = 0; r < 9; ++r) c.R_wc[r] = (float)Rm[r];
+            for (int r = 0; r < 3; ++r)
+                c.t_wc[r] = (float)-(Rm[3 * r] * cen[0] + Rm[3 * r + 1] * cen[1] + Rm[3 * r + 2] * cen[2]);
+            cams.push_back(c);
+            ox.push_back(i * chunk);
+            oy.push_back(j * chunk);
+        }
+    // scratch for one batch of full-size chunks
+    std::vector<rogs_camera> full(batch, cams[0]);
+    for (auto& c : full) { c.width = std::min(chunk, width); c.height = std::min(chunk, height); }
+    rogs_state_layout L;
+    uint64_t elems = 0;
+    rogs_status st = rogs_state_layout_of(ctx, full.data(), batch, &L, &elems);
+    if (st != ROGS_OK) return st;
+    st = grow(ctx, ctx->bev_out, ctx->bev_out_cap, (size_t)elems, s);
+    if (st == ROGS_OK) st = grow(ctx, ctx->bev_state, ctx->bev_state_cap, (size_t)L.total_bytes, s);
+    if (st != ROGS_OK) return st;
+    for (size_t b0 = 0; b0 < cams.size(); b0 += (size_t)batch) {
+        const int nb = (int)std::min<size_t>((size_t)batch, cams.size() - b0);
+        st = rogs_render_fwd(ctx, surfels, cams.data() + b0, nb, exposure_ab, n_exposure, ctx->bev_out,
+                             ctx->bev_state, stream);
+        if (st != ROGS_OK) return st;
+        rogs_counts cnt;
+        st = rogs_state_counts(ctx, ctx->bev_state, &cnt, stream);   // overflow check (synchronises)
+        if (st != ROGS_OK) return st;
+        StitchViews sv{};
+        long long acc = 0;
+        for (int v = 0; v < nb; ++v) {
+            const rogs_camera& c = cams[b0 + v];
+            acc += (long long)c.width * c.height;
+            sv.pix_end[v] = acc;
+            sv.w[v] = c.width;
+            sv.h[v] = c.height;
+            sv.x0[v] = ox[b0 + v];
+            sv.y0[v] = oy[b0 + v];
+        }
+        stitch_views(sv, nb, nch, ctx->bev_out, image, width, height, s);
+    }
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }

@@ -135,6 +135,15 @@ void project_bwd(const ViewParams* views, SurfelPtrs sp, const Record* recs, con
 void adam_step(const rogs_adam_group* groups, int n_groups, int step, float b1, float b2, float eps, bool zero_grad,
                cudaStream_t s);
 
+// ---- bev.cu
+constexpr int kMaxStitch = 16;   // chunk views per stitch launch
+struct StitchViews {
+    long long pix_end[kMaxStitch];   // exclusive prefix end of each view's pixels in the batch
+    int w[kMaxStitch], h[kMaxStitch], x0[kMaxStitch], y0[kMaxStitch];
+};
+void stitch_views(const StitchViews& sv, int n_views, int nch, const float* out, float* image, int W, int H,
+                  cudaStream_t s);
+
 // ---- lidar.cu
 struct LidarScratch {   // point-cloud hash: capacity m points, 2^lidar_bucket_bits(m) buckets
     uint32_t *keys, *vals, *skeys, *svals, *kalt, *valt, *hist;

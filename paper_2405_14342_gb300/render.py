@@ -173,6 +173,15 @@ class Renderer:
                                       self.grads_struct(grads), stream, lambda_smooth)
         return Graph(g, keep=(m, frame, exposure, tgt_rgb, label, mask, loss, grads))
 
+    def bev_export(self, m: SurfelTensors, exposure: torch.Tensor, x0, y1, res, width, height, chunk=2000,
+                   batch=4, cam_z=100.0, exposure_idx=0, stream=None) -> torch.Tensor:
+        """Chunked BEV export (rogs_bev_export): [3 + C + 1, height, width] planes
+        of the ground rectangle whose top-left corner is (x0, y1)."""
+        image = torch.empty((3 + self.C + 1, height, width), device=m.xyz.device)
+        R.rogs_bev_export(self.ctx, m.c_struct(), exposure, exposure_idx, x0, y1, res, cam_z, width, height, chunk,
+                          batch, image, stream)
+        return image
+
     def elev_targets(self, m: SurfelTensors, points: torch.Tensor, radius=0.1, stream=None) -> torch.Tensor:
         """LiDAR elevation targets zbar [n] (NaN where no point is within radius)."""
         zt = torch.empty(m.n, device=m.xyz.device)

@@ -136,6 +136,8 @@ def lib():
         L.rogs_smooth_loss.argtypes = [P, C.POINTER(rogs_surfels), C.c_float, P, P, P]
         L.rogs_elev_targets.argtypes = [P, C.POINTER(rogs_surfels), P, C.c_int64, C.c_float, P, P]
         L.rogs_elev_loss.argtypes = [P, C.POINTER(rogs_surfels), P, C.c_float, P, P, P]
+        L.rogs_bev_export.argtypes = [P, C.POINTER(rogs_surfels), P, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                      C.c_float, C.c_float, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P]
         L.rogs_adam_step.argtypes = [P, C.POINTER(rogs_adam_group), C.c_int32, C.c_int32, C.c_float, C.c_float,
                                      C.c_float, C.c_int32, P]
         L.rogs_train_step.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P, C.c_int32,
@@ -157,7 +159,7 @@ def lib():
         L.rogs_profile_read.argtypes = [P, C.POINTER(rogs_profile)]
         L.rogs_launch_count.argtypes = []
         L.rogs_launch_count.restype = C.c_uint64
-        for name in ("rogs_train_step", "rogs_smooth_loss", "rogs_adam_step", "rogs_elev_targets", "rogs_elev_loss",
+        for name in ("rogs_train_step", "rogs_smooth_loss", "rogs_adam_step", "rogs_elev_targets", "rogs_elev_loss", "rogs_bev_export",
                      "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
                      "rogs_serve_get_stats", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
                      "rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
@@ -297,6 +299,13 @@ def rogs_elev_targets(ctx, surf: rogs_surfels, points, radius, z_target, stream=
 def rogs_elev_loss(ctx, surf: rogs_surfels, z_target, lambda_z, loss, grad_xyz=None, stream=None):
     _check(ctx, lib().rogs_elev_loss(ctx, C.byref(surf), _ptr(z_target), float(lambda_z), _ptr(loss), _ptr(grad_xyz),
                                      _stream(stream)))
+
+
+def rogs_bev_export(ctx, surf: rogs_surfels, exposure_ab, exposure_idx, x0, y1, res, cam_z, width, height, chunk,
+                    batch, image, stream=None):
+    _check(ctx, lib().rogs_bev_export(ctx, C.byref(surf), _ptr(exposure_ab), int(exposure_ab.shape[0]),
+                                      int(exposure_idx), float(x0), float(y1), float(res), float(cam_z), int(width),
+                                      int(height), int(chunk), int(batch), _ptr(image), _stream(stream)))
 
 
 def rogs_adam_step(ctx, groups, step, beta1=0.9, beta2=0.999, eps=1e-8, zero_grad=True, stream=None):
