@@ -133,7 +133,10 @@ __global__ void __launch_bounds__(256) tile_keys_k(const uint2* __restrict__ ran
         }
         const uint2 r = ranges[t];
         const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-        keys[t] = 0xffffu - (len < 0xffffu ? len : 0xffffu);   // ascending key = descending length
+        // 8-bit logarithmic length class (steps of 2^(1/16), about 4 %, up to 2^16
+        // entries), ascending key = descending length: one radix pass orders the tiles
+        const float lc = 16.0f * __log2f(1.0f + (float)len);
+        keys[t] = 255u - (lc < 255.0f ? (uint32_t)lc : 255u);
         vals[t] = (uint32_t)t;
     }
 }
@@ -146,7 +149,7 @@ void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool s
     tile_keys_k<<<(int)blocks, 256, 0, s>>>(ranges, n_tiles, ka, va, order, sort_ok ? 1 : 0);
     note_launches(1);
     if (sort_ok)
-        radix_sort_pairs(ka, va, kb, order, kalt, vb, nullptr, (unsigned long long)n_tiles, 16, hist, s, sort_tile);
+        radix_sort_pairs(ka, va, kb, order, kalt, vb, nullptr, (unsigned long long)n_tiles, 8, hist, s, sort_tile);
 }
 
 }  // namespace rogs
