@@ -112,11 +112,30 @@ class ClockSampler:
 
 # --------------------------------------------------------------- workload
 
+RANK_STRIDE = 40   # timesteps between the first timesteps of consecutive ranks
+
+
+def rank_timesteps(rank: int, n_t: int):
+    """Timesteps of one rank: each rank takes its own stretch of road (weak
+    scaling); with n_t <= RANK_STRIDE the ranks' stretches do not overlap."""
+    t0 = T_FIRST + RANK_STRIDE * rank
+    return [t0 + k for k in range(n_t)]
+
+
+def max_over_ranks(value: float, world: int, dist, device="cuda") -> float:
+    """The slowest rank's time: all-reduce MAX (a no-op for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def build_workload(rank: int, C: int, world: int, n_t: int):
     from paper_2405_14342_gb300 import scenes
     m, field = scenes.strip_map(C=C, seed=0)
-    t0 = T_FIRST + 40 * rank          # each rank takes its own stretch of road (weak scaling)
-    rigs = [scenes.surround_rig(field, t0 + k) for k in range(n_t)]
+    rigs = [scenes.surround_rig(field, t) for t in rank_timesteps(rank, n_t)]
     return m, field, rigs
 
 
@@ -158,12 +177,7 @@ def _timed(fn, steps, world, dist):
         fn(k)
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    return max_over_ranks(e0.elapsed_time(e1), world, dist)
 
 
 def run_ours(args):
