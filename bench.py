@@ -5,9 +5,9 @@ Workload (default, "scene"): a 400 m x 40 m road strip at 0.1 m spacing
 (1.6M surfels, 19 semantic classes) on a smooth random height field; six
 960x540 surround pinhole cameras on a straight trajectory at 1.5 m height.
 One step = forward render of one timestep's six views (projection + cull,
-depth sort, tile binning and sort, compositing), the masked L1 + CE loss and
-the backward (reverse compositing + projection backward), all through the
-C-ABI of librogs.  Steps cycle over timesteps t = 8..39; the map and every
+depth sort, tile binning and sort, compositing), the masked L1 + CE loss, the
+grid smoothness loss and the backward (reverse compositing + projection
+backward), all through the C-ABI of librogs.  Steps cycle over timesteps t = 8..39; the map and every
 timestep's targets are resident in HBM before timing (inputs larger than L2).
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on

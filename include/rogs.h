@@ -243,7 +243,9 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
    FP32 summation order).  With lambda_smooth != 0 the step also takes the
    elevation smoothness loss of rogs_smooth_loss (needs surfels->grid_index),
    so loss[0] = lambda_c L_c + lambda_s L_s + lambda_smooth L_smooth (Eq. 12
-   without the LiDAR term).  Arguments as in those calls; gradients are ADDED
+   without the LiDAR term); that term runs on a stream owned by the context,
+   forked from and joined back into `stream` with events, beside the backward
+   compositing.  Arguments as in those calls; gradients are ADDED
    into `grads`; loss: device float[1]. */
 rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
                             const float* exposure_ab, int32_t n_exposure, float* out, void* state,

@@ -47,6 +47,8 @@ struct rogs_ctx {
     float* smooth_partials = nullptr;   // one per CTA of the smoothness-loss stencil
     float* smooth_val = nullptr;        // lambda_smooth L_smooth of the current training step
     float* elev_partials = nullptr;     // one per CTA of the LiDAR elevation loss
+    cudaStream_t side = nullptr;        // runs the smoothness loss beside the backward compositing
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     LidarScratch lidar{};               // point-cloud hash of rogs_elev_targets
     float* bev_out = nullptr;           // per-batch chunk outputs of rogs_bev_export
     uint8_t* bev_state = nullptr;
@@ -344,6 +346,10 @@ rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
     ROGS_ALLOC(ctx->smooth_partials, (size_t)smooth_blocks());
     ROGS_ALLOC(ctx->smooth_val, 1);
     ROGS_ALLOC(ctx->elev_partials, (size_t)elev_blocks());
+    if (st == ROGS_OK && (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess))
+        st = ROGS_ERR_CUDA;
 #undef ROGS_ALLOC
     (void)c0;
     if (st != ROGS_OK) {
@@ -369,6 +375,9 @@ void rogs_destroy(rogs_ctx* ctx) {
                     ctx->bev_state};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     for (const ProfEvent& pe : ctx->prof_pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);
@@ -662,9 +671,16 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
     prof_mark(ctx, 5, s);
     mask_count(mask, total_pix, ctx->loss_counter, s);
-    if (lambda_smooth != 0.0f)   // lambda_smooth L_smooth into a scalar the final loss sum adds, dz into the gradient
+    if (lambda_smooth != 0.0f) {
+        // lambda_smooth L_smooth into a scalar the final loss sum adds, dz into the
+        // gradient; independent of the rendering, so it runs on a side stream while
+        // the backward compositing runs (joined before the final loss sum)
+        ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+        ROGS_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
         smooth_loss(surfels->grid_index, surfels->grid_w, surfels->grid_h, surfels->xyz, lambda_smooth,
-                    ctx->smooth_val, grads->xyz, ctx->smooth_partials, s);
+                    ctx->smooth_val, grads->xyz, ctx->smooth_partials, ctx->side);
+        ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+    }
     BwdArgs a{};
     a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs;
     a.feat = (const float*)(sb + L.rec_feat);
@@ -682,6 +698,7 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
     prof_mark(ctx, 6, s);
     composite_bwd(cfg.tile_w, cfg.tile_h, total_tiles, a, s);
+    if (lambda_smooth != 0.0f) ROGS_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
     loss_final(ctx->loss_partials, n_partials, ctx->loss_counter, lambda_smooth != 0.0f ? ctx->smooth_val : nullptr,
                loss, s);
     prof_mark(ctx, 7, s);
