@@ -33,6 +33,9 @@ namespace rogs {
 int grad_channels(int C) { return padded_channels(C) <= 24 ? 32 : 64; }
 
 constexpr int kSubPad = 33;   // padded row stride of the per-warp tables
+// an entry's gradient row (mean 2, conic 3, alpha 1, 3 + C + 1 features) is
+// written over its two table rows in phase B
+static_assert(2 * kSubPad >= 6 + 3 + ROGS_MAX_CLASSES + 1, "a gradient row must fit the two table rows");
 constexpr int kBwdWarpsPerBlock = 2;
 
 template <int NCP>
@@ -296,9 +299,12 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
                 float* r0 = s_w + e * SP;
                 float* r1 = s_p + e * SP;
                 r0[0] = g0; r0[1] = g1; r0[2] = g2; r0[3] = g3; r0[4] = g4; r0[5] = g5 / cc.w;
+                // the padded channels are zero and never flushed; the widest rows
+                // (6 + 64 > 2 * SP) keep only the real ones, the others write all
 #pragma unroll
                 for (int ch = 0; ch < NCP; ++ch) {
                     const int col = 6 + ch;
+                    if (6 + NCP > 2 * SP && ch >= nch) break;
                     if (col < SP) r0[col] = acc[ch];
                     else r1[col - SP] = acc[ch];
                 }

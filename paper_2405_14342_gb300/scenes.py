@@ -316,7 +316,8 @@ def random_targets(cams: List[Camera], C: int, seed=3, mask_frac=0.8) -> Targets
         yy, xx = np.meshgrid(np.linspace(0, 1, H), np.linspace(0, 1, W), indexing="ij")
         rgb = np.clip(base + 0.3 * np.sin(6 * xx + 3 * yy)[None] + rng.normal(0, 0.05, (3, H, W)), 0, 1)
         rgbs.append(rgb.astype(np.float32))
-        labels.append(rng.integers(0, C, size=(H, W)).astype(np.int32))
+        labels.append(rng.integers(0, C, size=(H, W)).astype(np.int32) if C > 0
+                      else np.full((H, W), -1, np.int32))   # no classes: no semantic term
         masks.append((rng.uniform(0, 1, size=(H, W)) < mask_frac).astype(np.uint8))
     return Targets(rgbs, labels, masks)
 

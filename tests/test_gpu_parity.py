@@ -422,3 +422,15 @@ def test_init_rejects_degenerate_pose(R):
     with pytest.raises(rogs.RogsError) as ei:
         rr.init_from_poses(torch.zeros(4, 2, device="cuda"), poses, exact_plane=True)
     assert ei.value.status == rogs.ROGS_ERR_INVALID
+
+
+def test_extreme_class_counts(R):
+    """No semantic classes (8 padded channels) and 40 classes (64 padded
+    channels, the widest kernels): forward and backward against the oracle."""
+    cams = [scenes.tiny_camera()]
+    for C in (0, 40):
+        m = _generic_tiny(C=C)
+        rr = make(R, C)
+        compare_forward(R, rr, m, cams, np.zeros((1, 2), np.float32), depth_scale=[40.0])
+        tg = scenes.random_targets(cams, C, seed=8)
+        compare_backward(R, make(R, C), m, cams, np.array([[0.05, 0.01]], np.float32), tg)
