@@ -162,14 +162,13 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                 split_tf32(w1[0], ah[mt][2], al[mt][2]);
                 split_tf32(w1[8], ah[mt][3], al[mt][3]);
             }
+            uint32_t bh[NT][2], bl[NT][2];
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
-                uint32_t bh[2], bl[2];
-                split_tf32(s_f[(k0 + t) * SF + 8 * nt + g], bh[0], bl[0]);
-                split_tf32(s_f[(k0 + t + 4) * SF + 8 * nt + g], bh[1], bl[1]);
-                mma_tf32x3(acc[0][nt], ah[0], al[0], bh, bl);
-                mma_tf32x3(acc[1][nt], ah[1], al[1], bh, bl);
+                split_tf32(s_f[(k0 + t) * SF + 8 * nt + g], bh[nt][0], bl[nt][0]);
+                split_tf32(s_f[(k0 + t + 4) * SF + 8 * nt + g], bh[nt][1], bl[nt][1]);
             }
+            mma_tf32x3_tiles<NT>(acc, ah, al, bh, bl, true);
         }
         __syncwarp();
     }
