@@ -42,7 +42,7 @@ SM_COUNT, FP32_LANES = 152, 128   # GB300: 152 SMs x 128 FP32 lanes
 NCU_TRAFFIC = {
     # ncu --set full, one launch of the scene workload (6 x 960x540) per tile shape; see profiles/
     "composite_bwd": {"sha": "42ccde2bbe9e2e0d", "16x16": 296_062_464 + 54_396_160, "8x8": 325_580_800 + 55_118_080},
-    "composite_fwd": {"sha": "e2984185268c3548", "16x16": 74_577_664 + 256_334_848, "8x8": 105_059_328 + 258_623_488},
+    "composite_fwd": {"sha": "3bbe607479798965", "16x16": 74_588_160 + 255_846_400},
 }
 
 

@@ -66,6 +66,14 @@ def compare_forward(R, rr, m, cams, ex, depth_scale, max_band_frac=1e-4, max_ban
     assert e_sem < TOL_RGB, e_sem
     assert e_dep < TOL_RGB, e_dep
     assert e_T < TOL_RGB, e_T
+    # E, the composited (pixel, surfel) pairs the forward counts, against the
+    # oracle's per-pixel counts: equal unless a pixel sits in the ambiguity
+    # band, where a threshold or stop decision may go either way
+    e_ref = int(ref.ncomp.sum())
+    if n_band == 0:
+        assert int(cnt.composited) == e_ref
+    else:
+        assert abs(int(cnt.composited) - e_ref) <= 64 * n_band, (int(cnt.composited), e_ref, n_band)
     return st, fr, ext, cnt, ref, pix
 
 
