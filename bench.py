@@ -425,6 +425,18 @@ def run_ours(args):
         "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"
     roof["duration_ms"] = round(stage_ms[dom], 4)
     roof["work_per_launch"] = {"bytes": round(b), "flops": round(f)}
+    # both terms of the dominant kernel, and the binding term of every stage
+    roof["terms"] = {"hbm": {"achieved_gbs": round(b / t / 1e9, 1), "peak": hbm,
+                             "frac": round(b / t / 1e9 / hbm, 4)},
+                     "alu": {"achieved_tflops": round(f / t / 1e12, 3), "peak": round(alu_peak, 2),
+                             "frac": round(f / t / 1e12 / alu_peak, 4)}}
+    stage_roof = {}
+    for k, ms_k in stage_ms.items():
+        bk, fk = stage_work[k]
+        tk = ms_k * 1e-3
+        fr_h, fr_a = bk / tk / 1e9 / hbm, fk / tk / 1e12 / alu_peak
+        stage_roof[k] = {"bound": "alu" if fk / alu_peak / 1e12 > bk / hbm / 1e9 else "hbm",
+                         "hbm_frac": round(fr_h, 4), "alu_frac": round(fr_a, 4)}
     src = os.path.join(ROOT, "paper_2405_14342_gb300", "csrc",
                        "backward.cu" if dom in ("composite_bwd", "project_bwd") else "composite.cu")
     tr = NCU_TRAFFIC.get(dom)
@@ -455,6 +467,7 @@ def run_ours(args):
         },
         "roofline": roof,
         "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof.items()},
+        "stages_roofline": stage_roof,
         "counts_per_step": {"records": round(nr), "pairs": round(K), "composited": round(E)},
         "gpu_launches": int(launches),
         "lidar_supervision": lidar,
@@ -591,7 +604,7 @@ def numpy_targets(cams, C, seed=3):
     return scenes.random_targets(cams, C, seed=seed)
 
 
-def cpu_baseline(args, rigs=None, budget_s=20.0):
+def cpu_baseline(args, rigs=None, budget_s=20.0, single_core_s=6.0):
     """The oracle as it stands on this host's cores, on a bounded pixel sample
     of the bench workload (time = fixed projection cost + per-pixel cost; the
     sample size is chosen from two calibration runs to fill `budget_s`)."""
@@ -612,9 +625,23 @@ def cpu_baseline(args, rigs=None, budget_s=20.0):
     t0 = time.time()
     npx, _ = oracle_step(m, cams, ex, tg, per, seed=1)
     dt = time.time() - t0
-    return {"value": round(npx / dt / 1e6, 6), "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{per} random road-half pixels per view x 6 views of timestep {T_FIRST} "
-                      f"(fwd+loss+bwd, FP64 brute force over all 1.6M surfels), {dt:.1f} s"}
+    out = {"value": round(npx / dt / 1e6, 6), "unit": "Mpix/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{per} random road-half pixels per view x 6 views of timestep {T_FIRST} "
+                     f"(fwd+loss+bwd, FP64 brute force over all 1.6M surfels), {dt:.1f} s"}
+    # the same on one core, on a sample sized from the all-core per-pixel cost
+    cores = oracle.num_threads()
+    if single_core_s > 0 and cores > 1:
+        oracle.set_threads(1)
+        try:
+            per1 = int(max(16, min(per, single_core_s / (per_px * cores))))
+            t0 = time.time()
+            n1, _ = oracle_step(m, cams, ex, tg, per1, seed=2)
+            dt1 = time.time() - t0
+        finally:
+            oracle.set_threads(cores)
+        out["single_core"] = {"value": round(n1 / dt1 / 1e6, 6), "cores": 1,
+                              "sample": f"{per1} pixels per view x 6 views, {dt1:.1f} s"}
+    return out
 
 
 def run_reference(args):
