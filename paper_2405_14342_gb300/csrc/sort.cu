@@ -1,5 +1,5 @@
 // sort.cu -- hand-written stable LSD radix sort of (uint32 key, uint32 value)
-// pairs with a device-resident length (8-bit digits, 4096-key tiles).
+// pairs with a device-resident length (8-bit digits, 2048-8192 keys per CTA).
 //
 // Keys per CTA (the sort "chunk") is 2048, 4096 or 8192 (8/16/32 keys per
 // thread), chosen by the context configuration.  Per pass, three launches
