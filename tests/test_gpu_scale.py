@@ -2,7 +2,10 @@
 outputs, plus the equalities that must hold at any size:
 
 * scene config (1.6M surfels, 6 x 960x540): sampled pixels (road half and a
-  band of horizon rows, where tile lists are longest) at 1e-4;
+  band of horizon rows, where tile lists are longest) at 1e-4; and the fused
+  training step (loss + backward + grid smoothness, the bench's tile and sort
+  chunk) with the loss mask on a pixel sample, every gradient tensor against
+  the FP64 oracle (1e-3 normwise);
 * batching config (48 views of uneven size in one call): every view equals
   the same view rendered alone, bit for bit, and sampled pixels match the
   oracle;
@@ -78,6 +81,53 @@ def test_scene_config_sampled_pixels(R, strip):
     ref = oracle.render(m, cams, ex, pix)
     assert (ref.T < 0.5).sum() > len(pix) // 3      # the sample does hit the road
     check_pixels(fr, 19, ref, pix)
+
+
+def test_scene_config_training_step_gradients(R, strip):
+    """The bench's training step at full size (1.6M surfels, six 960x540 views,
+    16x16 tiles, 2048-key sort chunks; loss fused into the backward, plus the
+    grid smoothness term) against the FP64 oracle.  The loss mask holds a
+    sample of pixels only, so the exact gradient depends on those pixels alone
+    and the oracle computes it by brute force over every surfel.  Sampled
+    pixels in the ambiguity band, or with a colour within 1e-3 of its target
+    (where the L1 sign could differ between FP32 and FP64), are left out."""
+    m, field = strip
+    C = 19
+    cams = scenes.surround_rig(field, 8)
+    ex = scenes.exposure_params(6)
+    gi = scenes.grid_index(m)
+    tg = scenes.random_targets(cams, C, seed=5)
+    pix = np.unique(sample_pixels(cams, 100, seed=4), axis=0)   # each masked pixel once
+    ref = oracle.render(m, cams, ex, pix)
+    rgb_t, _, _ = oracle.gather_targets(tg, pix)
+    keep = (ref.amb == 0) & (np.abs(ref.out[:, :3] - rgb_t).min(1) > 1e-3)
+    pix = pix[keep]
+    assert len(pix) > 400
+    for v in range(len(cams)):
+        tg.mask[v][:] = 0
+    for v, u, y in pix:
+        tg.mask[v][y, u] = 1
+    rr = R.Renderer(C, record_capacity=2_000_000, pair_capacity=12_000_000, tile=(16, 16), sort_tile=2048)
+    st = R.SurfelTensors.from_map(m, grid_index=gi)
+    exd = torch.as_tensor(ex, device="cuda")
+    trgb, lab, msk = R.targets_to_device(tg)
+    fr = rr.frame(cams)
+    loss = torch.empty(1, device="cuda")
+    grads = R.zero_grads(st, exd)
+    lam = 0.003
+    rr.train_step(st, fr, exd, trgb, lab, msk, loss, grads, lambda_smooth=lam)
+    torch.cuda.synchronize()
+    L, g, _ = oracle.loss_and_grads(m, cams, ex, tg, pix)
+    Ls, gs = oracle.smooth_loss(m.xyz[:, 2].astype(np.float64), gi)
+    assert abs(loss.item() - (L + lam * Ls)) <= 1e-5 * abs(L + lam * Ls)
+    ref_g = g.as_dict()
+    ref_g["xyz"] = ref_g["xyz"].copy()
+    ref_g["xyz"][:, 2] += lam * gs
+    errs = {}
+    for k in ("xyz", "scale", "quat", "opacity", "rgb", "sem", "exposure"):
+        a = grads[k].cpu().numpy().astype(np.float64).reshape(ref_g[k].shape)
+        errs[k] = normwise(a, ref_g[k])
+    assert all(e <= 1e-3 for e in errs.values()), errs
 
 
 def test_batching_config_matches_single_views_and_oracle(R, strip):
