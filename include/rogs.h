@@ -218,8 +218,9 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
        + lambda_s/|M| sum_i m_i CE(softmax(sem_i), label_i)
    |M| = number of mask pixels (L = 0 and zero gradient if |M| = 0).
    out: the forward output; tgt_rgb: device [3][pixels] planes per view (same
-   pixel offsets as out); label: device int32 [pixels] in [0, C); mask:
-   device uint8 [pixels] (a label outside [0, C) drops that pixel's semantic term).  Writes loss: device float[1] and grad_out: device
+   pixel offsets as out); label: device int32 [pixels] in [0, C) (a label
+   outside [0, C) drops that pixel's semantic term); mask: device uint8
+   [pixels].  Writes loss: device float[1] and grad_out: device
    float[out_elems] = dL/dout (depth plane zero; sign(0) = 0 for L1). */
 rogs_status rogs_loss(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, const float* out,
                       const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
