@@ -122,6 +122,16 @@ void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Re
     note_launches(1);
 }
 
+// Tile schedule key: an 8-bit logarithmic length class (steps of 2^(1/16),
+// about 4 %, up to 2^16 entries), ascending key = descending list length, so
+// one stable pass over it gives the longest-list-first order.
+__device__ __forceinline__ uint32_t tile_class_key(const uint2* __restrict__ ranges, long long t) {
+    const uint2 r = ranges[t];
+    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+    const float lc = 16.0f * __log2f(1.0f + (float)len);
+    return 255u - (lc < 255.0f ? (uint32_t)lc : 255u);
+}
+
 __global__ void __launch_bounds__(256) tile_keys_k(const uint2* __restrict__ ranges, long long n_tiles,
                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    uint32_t* __restrict__ order, int sort_ok) {
@@ -131,18 +141,102 @@ __global__ void __launch_bounds__(256) tile_keys_k(const uint2* __restrict__ ran
             order[t] = (uint32_t)t;
             continue;
         }
-        const uint2 r = ranges[t];
-        const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-        // 8-bit logarithmic length class (steps of 2^(1/16), about 4 %, up to 2^16
-        // entries), ascending key = descending length: one radix pass orders the tiles
-        const float lc = 16.0f * __log2f(1.0f + (float)len);
-        keys[t] = 255u - (lc < 255.0f ? (uint32_t)lc : 255u);
+        keys[t] = tile_class_key(ranges, t);
         vals[t] = (uint32_t)t;
+    }
+}
+
+// The same stable order in one block when the frame has few tiles: a
+// counting sort on the class key.  Warp w owns the w-th contiguous segment of
+// tiles; (1) each warp counts its segment's keys, (2) digit-major exclusive
+// offsets over (digit, warp), (3) each warp scatters its segment in order,
+// ranking equal keys inside 32-tile steps by lane.  No block waits on
+// another; one launch replaces the key kernel and a three-launch radix pass.
+constexpr int kOrderThreads = 1024;
+constexpr long long kOrderOneBlockMax = 32768;
+
+__global__ void __launch_bounds__(kOrderThreads) tile_order_block_k(const uint2* __restrict__ ranges,
+                                                                    long long n_tiles,
+                                                                    uint32_t* __restrict__ order) {
+    __shared__ uint32_t wh[kOrderThreads / 32][256];   // per-warp counts, then write positions
+    __shared__ uint32_t scan_w[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    const long long per = (n_tiles + 31) / 32;
+    const long long beg = (long long)warp * per;
+    const long long end = beg + per < n_tiles ? beg + per : n_tiles;
+    for (int i = threadIdx.x; i < 32 * 256; i += kOrderThreads) (&wh[0][0])[i] = 0u;
+    __syncthreads();
+    for (long long b = beg; b < end; b += 32) {   // (1)
+        const long long t = b + lane;
+        const bool valid = t < end;
+        const unsigned vm = __ballot_sync(kFull, valid);
+        if (valid) {
+            const uint32_t d = tile_class_key(ranges, t);
+            const unsigned peers = __match_any_sync(vm, d);
+            if ((peers & lt) == 0u) wh[warp][d] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tot = 0, inc = 0;   // (2): thread d < 256 owns digit d
+    if (threadIdx.x < 256) {
+        const int d = threadIdx.x;
+        for (int w = 0; w < 32; ++w) tot += wh[w][d];
+        inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += x;
+        }
+        if (lane == 31) scan_w[warp] = inc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t c = 0;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t x = scan_w[w];
+            scan_w[w] = c;
+            c += x;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+        const int d = threadIdx.x;
+        uint32_t run = scan_w[warp] + inc - tot;
+        for (int w = 0; w < 32; ++w) {
+            const uint32_t c = wh[w][d];
+            wh[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (long long b = beg; b < end; b += 32) {   // (3)
+        const long long t = b + lane;
+        const bool valid = t < end;
+        const unsigned vm = __ballot_sync(kFull, valid);
+        uint32_t d = 0;
+        unsigned peers = 0;
+        if (valid) {
+            d = tile_class_key(ranges, t);
+            peers = __match_any_sync(vm, d);
+            order[wh[warp][d] + __popc(peers & lt)] = (uint32_t)t;
+        }
+        __syncwarp();
+        if (valid && (peers & lt) == 0u) wh[warp][d] += __popc(peers);
+        __syncwarp();
     }
 }
 
 void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool sort_ok, uint32_t* ka, uint32_t* va,
                  uint32_t* kb, uint32_t* vb, uint32_t* kalt, uint32_t* hist, cudaStream_t s, int sort_tile) {
+    if (sort_ok && n_tiles <= kOrderOneBlockMax) {
+        if (n_tiles > 0) {
+            tile_order_block_k<<<1, kOrderThreads, 0, s>>>(ranges, n_tiles, order);
+            note_launches(1);
+        }
+        return;
+    }
     long long blocks = (n_tiles + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;

@@ -23,7 +23,7 @@ from paper_2405_14342_gb300 import scenes
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from _util import gpu_pixels, gpu_state_T, normwise, pixel_index, planar_grad_from_pixels  # noqa: E402
+from _util import gpu_pixels, gpu_state_T, gpu_tile_lists, normwise, pixel_index, planar_grad_from_pixels  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -128,6 +128,39 @@ def test_scene_config_training_step_gradients(R, strip):
         a = grads[k].cpu().numpy().astype(np.float64).reshape(ref_g[k].shape)
         errs[k] = normwise(a, ref_g[k])
     assert all(e <= 1e-3 for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_tile_order_is_longest_first_and_stable(R, strip, tile):
+    """The compositing kernels take tiles longest list first.  12,240 tiles
+    (16x16) are ordered by the one-block counting sort, 48,960 (8x8) by the
+    radix pass; both give a permutation in which list lengths fall by at most
+    one length class (2^(1/16)) step at a time and equal lengths keep the
+    tile index order."""
+    m, field = strip
+    cams = scenes.surround_rig(field, 8)
+    rr = R.Renderer(19, record_capacity=2_000_000, pair_capacity=12_000_000, tile=tile)
+    st = R.SurfelTensors.from_map(m)
+    fr = rr.frame(cams)
+    rr.forward(st, fr, torch.as_tensor(scenes.exposure_params(6), device="cuda"))
+    torch.cuda.synchronize()
+    cnt = rr.counts(fr)
+    T = int(fr.layout.total_tiles)
+    assert (T <= 32768) == (tile == (16, 16))
+    order = fr.state_section("tile_order", torch.int32, T).cpu().numpy().astype(np.int64)
+    _, rg = gpu_tile_lists(fr, cnt)
+    length = (rg[:, 1] - rg[:, 0]).clip(min=0)
+    np.testing.assert_array_equal(np.sort(order), np.arange(T))
+    lo = length[order]
+    # classes are floor(16 log2(1 + len)): a later tile is never longer than one class step
+    assert np.all(np.log2(1.0 + lo[1:]) <= np.log2(1.0 + lo[:-1]) + 1.0 / 16 + 1e-6)
+    assert lo[0] == length.max() or np.log2(1.0 + length.max()) - np.log2(1.0 + lo[0]) < 1.0 / 16
+    # equal lengths keep index order: sorting the order by length (stably) must
+    # leave the indices of each length ascending
+    srt = order[np.argsort(lo, kind="stable")]
+    ls = np.sort(lo, kind="stable")
+    same = ls[1:] == ls[:-1]
+    assert np.all(np.diff(srt)[same] > 0)
 
 
 def test_batching_config_matches_single_views_and_oracle(R, strip):
