@@ -7,11 +7,15 @@ from paper_2405_14342_gb300 import scenes
 
 
 def test_single_point_and_radius():
-    xy = np.array([[0.0, 0.0], [0.3, 0.0], [1.0, 1.0]])
+    xy = np.array([[0.0, 0.0], [0.3, 0.0], [1.0, 1.0], [0.7, 0.0]])
     pts = np.array([[0.1, 0.0, 2.5]])
     zb, idx = oracle.nearest_elevation(xy, pts, radius=0.5)
     np.testing.assert_array_equal(zb[:2], [2.5, 2.5])
     assert np.isnan(zb[2]) and idx[2] == -1
+    assert np.isnan(zb[3]) and idx[3] == -1      # 0.6 m away: outside 0.5 m (though 0.6^2 < 0.5)
+    # a radius above 1 m: 1.5 m away is inside 2 m (though 1.5^2 > 2)
+    zb2, idx2 = oracle.nearest_elevation(np.array([[1.6, 0.0]]), pts, radius=2.0)
+    assert zb2[0] == 2.5 and idx2[0] == 0
 
 
 def test_points_on_the_surfels_pick_their_own():
