@@ -748,7 +748,9 @@ def run_ablation(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 800 for this implementation, about 1 s of graph replays so "
+                         "that the clock sampler sees the timed region under load; 32 for the oracle arm)")
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", default="auto", help="auto (autotuner) or WxH")
@@ -767,6 +769,8 @@ def main():
     ap.add_argument("--ablation", action="store_true", help="run the initialisation ablation instead of the bench")
     ap.add_argument("--ablation-iters", type=int, default=400)
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 800 if args.impl == "ours" and not args.ablation else 32
     if args.warmup < 3 and args.impl == "ours" and args.steps > 2:
         args.warmup = 3
     if args.ablation:
