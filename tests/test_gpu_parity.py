@@ -144,6 +144,34 @@ def test_records_match_oracle_projection(R):
     assert outside.all()
 
 
+def test_box_cull_matches_hand_worked_geometry(R):
+    """The kernels' perspective box cull against the hand-worked ground boxes of
+    the oracle pins (supplementary box cull): every record's surfel lies in its
+    camera's box, and every surfel in the box without a record has a footprint
+    entirely off the image."""
+    import test_oracle_box as box
+    for yaw, pitch, roll, cxy in box.CASES:
+        xh, zh = box.hand_ground_axes(yaw, pitch, roll)
+        m, LF, keep = box.box_map(cxy, xh, zh)
+        cam = box.box_camera(yaw, pitch, roll, cxy)
+        rr = make(R, m.num_classes)
+        st, fr, ext, cnt = gpu_render(R, rr, m, [cam], np.zeros((1, 2)))
+        rec = gpu_records(fr, cnt)
+        s = rec["surfel"].astype(np.int64)
+        assert keep[s].all(), [tuple(LF[i]) for i in s[~keep[s]]]
+        pr = oracle.project(m, [cam])
+        have = np.zeros(m.n, bool)
+        have[s] = True
+        miss = np.nonzero(keep & ~have)[0]
+        kappa = 2 * np.log(m.opacity[miss] / np.float32(1 / 255))
+        rx = np.sqrt(kappa * pr.cov[0, miss, 0]); ry = np.sqrt(kappa * pr.cov[0, miss, 2])
+        mx = pr.mu[0, miss, 0]; my = pr.mu[0, miss, 1]
+        outside = (mx + rx < 0.5) | (mx - rx > cam.width - 0.5) | (my + ry < 0.5) | (my - ry > cam.height - 0.5)
+        assert outside.all()
+        assert len(s) >= 8   # the box's far part is on the image
+        rr.close()
+
+
 def test_tile_lists_are_bit_exact(R):
     m = scenes.tiny_map()
     cams = [scenes.tiny_camera(), scenes.bev_camera((3.1, 3.2), 100, res_m=0.05, height_m=20.0)]

@@ -12,6 +12,7 @@ import tempfile
 import pytest
 
 import oracle
+import test_oracle_box as box
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "rogs_oracle.c")
@@ -44,6 +45,19 @@ MUTATIONS = {
     "jacobian_depth_term_dropped": ("J[0][2] = -c->fx * u / z;", "J[0][2] = 0;"),
     "mean_gradient_missing_offdiag": ("gg[0] += dpow * (o->con[0] * dx + o->con[1] * dy);",
                                       "gg[0] += dpow * (o->con[0] * dx);"),
+    # perspective box cull (supplementary "Perspective Rendering Acceleration")
+    "box_axes_swapped": ("float l0 = dx * c->xh0;\n    float l1 = dy * c->xh1;",
+                         "float l0 = dx * c->zh0;\n    float l1 = dy * c->zh1;"),
+    "box_forward_sign": ("float fwd = f0 + f1;", "float fwd = -(f0 + f1);"),
+    "box_sizes_swapped": ("(fabsf(lat) <= cfg->f_box_hx) && (fwd >= 0.0f) && (fwd <= cfg->f_box_d)",
+                          "(fabsf(lat) <= cfg->f_box_d) && (fwd >= 0.0f) && (fwd <= cfg->f_box_hx)"),
+    "box_forward_axis_unnormalised": ("c->zh0 = c->fR[6] / nz; c->zh1 = c->fR[7] / nz;",
+                                      "c->zh0 = c->fR[6]; c->zh1 = c->fR[7];"),
+    "box_lateral_axis_unnormalised": ("c->xh0 = c->fR[0] / nx; c->xh1 = c->fR[1] / nx;",
+                                      "c->xh0 = c->fR[0]; c->xh1 = c->fR[1];"),
+    "box_lateral_axis_from_column": ("c->xh0 = c->fR[0] / nx; c->xh1 = c->fR[1] / nx;",
+                                     "c->xh0 = c->fR[0] / nx; c->xh1 = c->fR[3] / nx;"),
+    "box_centre_sign": ("c->ox = -s;", "c->ox = s;"),
 }
 
 PIN_CALLS = [
@@ -59,6 +73,9 @@ PIN_CALLS = [
     pins.test_init_on_tilted_plane_is_exact,
     pins.test_init_yaw_only_and_small_roll_reading,
     pins.test_gradient_matches_central_differences,
+    *[(lambda c=c: box.test_box_cull_keeps_exactly_the_hand_worked_box(c)) for c in box.CASES],
+    box.test_box_cull_pitched_camera_needs_normalised_forward_axis,
+    box.test_box_cull_rolled_camera_needs_normalised_lateral_axis,
 ]
 
 
