@@ -454,16 +454,19 @@ void rogs_graph_destroy(rogs_graph* graph);
    are not modified; keys_out/vals_out must not overlap the inputs.
    Scratch: a fixed array of 2 * ROGS_NOALLOC_MAX_PAIRS + 131328 uint32
    (about 8.9 MB) compiled into the library's device image; every GPU that
-   loads the library holds it until the process exits.  The first call on a
-   device looks the array's device address up (cudaGetSymbolAddress) and
-   caches it: make that first call before any stream capture on that device.
+   loads the library holds it until the process exits.  Every call looks the
+   array's device address up in the current context (cudaGetSymbolAddress);
+   the first call on a device also loads the library's device code there, so
+   make that first call before any stream capture on that device.
    All calls share the one array, so calls whose executions overlap on the
    GPU (different streams, or concurrent host threads) race and corrupt each
    other's results; serialise them.  Nothing in the array needs clearing
    between calls.  Errors: ROGS_ERR_CAPACITY if n > ROGS_NOALLOC_MAX_PAIRS,
    ROGS_ERR_INVALID for n < 0, key_bits outside [0, 32] or a NULL pointer
-   with n > 0, ROGS_ERR_CUDA if the address lookup or a launch fails.  The
-   current device must be the device of `stream`. */
+   with n > 0, ROGS_ERR_CUDA if the address lookup or a launch fails during
+   this call (a CUDA error already pending when the call starts is neither
+   reported nor cleared here).  The current device must be the device of
+   `stream`. */
 rogs_status rogs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* vals_in, int64_t n, int32_t key_bits,
                                     uint32_t* keys_out, uint32_t* vals_out, rogs_stream stream);
 

@@ -13,9 +13,11 @@
 //
 // The host side of this file must not pass the array's name to a kernel: in
 // host code that name denotes a host-side shadow, not the device copy.  The
-// device address is looked up once per device with cudaGetSymbolAddress (the
-// first call on each device does it) and cached.
-#include <mutex>
+// device address is looked up with cudaGetSymbolAddress on every call, with
+// the caller's device current: the lookup is a host-side table read once the
+// library's device code is loaded (the first call on a device loads it), and
+// no address is kept across calls, so a context that was reset and re-created
+// (where the array may sit elsewhere) is never handed a stale address.
 
 #include "kernels.h"
 
@@ -31,24 +33,12 @@ constexpr unsigned long long kNoallocWords = 2ull * kNoallocMaxPairs + kNoallocH
 static __device__ __align__(256) uint32_t g_sort_scratch[kNoallocWords];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-uint32_t* g_dev_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_sort_scratch on the current device (looked up once).
+// Device address of g_sort_scratch in the current device's context.
 cudaError_t scratch_on_current_device(uint32_t** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_sort_scratch);
-        if (e != cudaSuccess) return e;
-        g_dev_ptr[dev] = static_cast<uint32_t*>(p);
-    }
-    *out = g_dev_ptr[dev];
+    *out = static_cast<uint32_t*>(p);
     return cudaSuccess;
 }
 }  // namespace
@@ -63,8 +53,15 @@ extern "C" rogs_status rogs_sort_pairs_noalloc(const uint32_t* keys_in, const ui
     if ((unsigned long long)n > kNoallocMaxPairs) return ROGS_ERR_CAPACITY;
     if (n == 0) return ROGS_OK;
     if (!keys_in || !vals_in || !keys_out || !vals_out) return ROGS_ERR_INVALID;
+    // an error already pending from some earlier, unrelated call is left for
+    // its owner: only an error that appears during this call is reported (and
+    // consumed) here
+    const bool clean_on_entry = cudaPeekAtLastError() == cudaSuccess;
     uint32_t* base = nullptr;
-    if (scratch_on_current_device(&base) != cudaSuccess) return ROGS_ERR_CUDA;
+    if (scratch_on_current_device(&base) != cudaSuccess) {
+        if (clean_on_entry) (void)cudaGetLastError();
+        return ROGS_ERR_CUDA;
+    }
     // Every histogram word the sort reads is written earlier in the same pass,
     // so nothing in the shared array has to be cleared between calls.
     uint32_t* kalt = base;
@@ -73,5 +70,9 @@ extern "C" rogs_status rogs_sort_pairs_noalloc(const uint32_t* keys_in, const ui
     static_assert(kNoallocHistWords >= 256ull * ((kNoallocMaxPairs + 2047ull) / 2048ull) + 256ull, "histogram room");
     radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, kalt, valt, nullptr, (unsigned long long)n, key_bits, hist,
                      (cudaStream_t)stream, 4096);
-    return cudaGetLastError() == cudaSuccess ? ROGS_OK : ROGS_ERR_CUDA;
+    if (clean_on_entry && cudaPeekAtLastError() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ROGS_ERR_CUDA;
+    }
+    return ROGS_OK;
 }
