@@ -260,10 +260,10 @@ def run_ours(args):
     # ---- optimiser step (outside the metric): one fused Adam step over every
     # learnt tensor of the map (z, opacity, scale, quat, rgb, sem) and the exposure
     st_opt = R.SurfelTensors(*[t.clone() for t in st.tensors()])   # the timed forms keep the original map
-    opt = R.Adam(rr, st_opt, exposure.clone())
+    opt = R.Adam(rr, st_opt, exposure.clone(), scene_size=400.0, total_steps=1000)
     for k in range(args.warmup):
-        opt.step(grads, R.z_lr(k, 1000, 400.0))
-    ms_adam = _timed(lambda k: opt.step(grads, R.z_lr(k, 1000, 400.0)), args.steps, world, dist) / args.steps
+        opt.step(grads)
+    ms_adam = _timed(lambda k: opt.step(grads), args.steps, world, dist) / args.steps
     adam_elems = sum(v[0].numel() for v in opt.state.values())
     del opt, st_opt
 
@@ -720,7 +720,7 @@ def run_ablation(args):
         st.quat.copy_(q0)
         st.rgb.fill_(0.5)
         st.sem.zero_()
-        opt = R.Adam(rr, st, exposure.clone())
+        opt = R.Adam(rr, st, exposure.clone(), scene_size=40.0, total_steps=K)
         grads = R.zero_grads(st, opt.exposure)
         fr = [rr.frame(c) for c in rigs]
         loss = torch.empty(1, device="cuda")
@@ -733,7 +733,7 @@ def run_ablation(args):
                 break
             j = k % n_t
             rr.train_step(st, fr[j], opt.exposure, *targets[j], loss, grads, lambda_smooth=LAMBDA_SMOOTH)
-            opt.step(grads, R.z_lr(k, K, 40.0))
+            opt.step(grads)
         res[name] = curve
         del st, opt, grads, fr
     return {"metric": "elevation RMSE (m) over the seen surfels vs training iterations",

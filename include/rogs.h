@@ -311,7 +311,16 @@ rogs_status rogs_elev_loss(rogs_ctx* ctx, const rogs_surfels* surfels, const flo
    param[k * stride] with gradient grad[k * stride] (stride 1 for a whole
    tensor; param = xyz + 2, grad = grad_xyz + 2, stride 3 for the z column
    only); m and v are its Adam moments, dense device float[n], zero before the
-   first step; lr its learning rate. */
+   first step.
+   Learning rate at step t (Sec. 4.2): lr when decay_steps == 0; otherwise the
+   rate falls log-linearly from lr to lr_end over decay_steps steps and stays
+   at lr_end, lr_t = lr (lr_end / lr)^min((t - 1) / decay_steps, 1) (the paper
+   gives only the two ends of z's rate, 1.6e-4 and 1.6e-6 times the scene
+   size; the shape between them is this library's reading).
+   zero_lead (0 <= zero_lead < stride): when the step clears gradients, it
+   also clears the zero_lead gradient floats just before each element -- for
+   the z column of xyz, 2 clears dL/dx and dL/dy, which Sec. 4.2 does not
+   learn. */
 typedef struct {
     float* param;
     float* grad;
@@ -320,19 +329,25 @@ typedef struct {
     int64_t n;
     int32_t stride;
     float lr;
+    float lr_end;
+    int32_t decay_steps;
+    int32_t zero_lead;
 } rogs_adam_group;
 
 #define ROGS_MAX_ADAM_GROUPS 16
 
 /* One Adam step (Sec. 4.2: Adam with per-tensor learning rates) over up to
    ROGS_MAX_ADAM_GROUPS groups in a single launch, at step number `step` >= 1
-   (bias correction): per element
+   (bias correction and the learning-rate schedule): per element
      m = b1 m + (1-b1) g,  v = b2 v + (1-b2) g^2,
-     p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
-   With zero_grad != 0 every gradient element is set to 0 after it is read,
-   ready for the next backward (which adds).  Groups must not overlap.
+     p -= lr_t (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+   With zero_grad != 0 every gradient element (and its zero_lead leading
+   floats) is set to 0 after it is read, ready for the next backward (which
+   adds).  Groups must not overlap.
    Errors: ROGS_ERR_INVALID for n_groups outside [1, ROGS_MAX_ADAM_GROUPS],
-   step < 1, stride < 1, n < 0 or a NULL pointer in a group with n > 0. */
+   step < 1, stride < 1, zero_lead outside [0, stride), decay_steps < 0,
+   lr or lr_end <= 0 with decay_steps > 0, n < 0 or a NULL pointer in a group
+   with n > 0. */
 rogs_status rogs_adam_step(rogs_ctx* ctx, const rogs_adam_group* groups, int32_t n_groups, int32_t step, float beta1,
                            float beta2, float eps, int32_t zero_grad, rogs_stream stream);
 

@@ -8,9 +8,14 @@
 // and aligned) and finds its group from the prefix offsets.  Per element:
 //   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
 //   p <- p - lr (m c1) / (sqrt(v c2) + eps),  c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
-// and optionally g <- 0 for the next backward, which adds into it.  The
-// step is bound by HBM: 16 bytes read and 12 (16 with the zeroing) written per
+// and optionally g <- 0 for the next backward, which adds into it (with the
+// group's zero_lead floats before g: the x and y gradients of the z column,
+// which Sec. 4.2 does not learn).  Each group's learning rate for this step
+// (constant, or z's log-linear decay from lr to lr_end) is evaluated on the
+// host in double before the launch.  The step is bound by HBM: 16 bytes read and 12 (16 with the zeroing) written per
 // element.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace rogs {
@@ -61,7 +66,10 @@ __global__ void __launch_bounds__(256) adam_k(AdamArgs a) {
                 G.param[pi] = p;
                 G.m[e] = m;
                 G.v[e] = v;
-                if (a.zero_grad) G.grad[pi] = g;
+                if (a.zero_grad) {
+                    G.grad[pi] = g;
+                    for (int j = 1; j <= G.zero_lead; ++j) G.grad[pi - j] = 0.0f;
+                }
             }
         }
     }
@@ -76,8 +84,12 @@ void adam_step(const rogs_adam_group* groups, int n_groups, int step, float b1, 
     for (int i = 0; i < n_groups; ++i) {
         const rogs_adam_group& g = groups[i];
         a.g[i] = g;
+        if (g.decay_steps > 0) {   // lr_t = lr (lr_end / lr)^min((t - 1) / decay_steps, 1)
+            const double f = std::min(1.0, (double)(step - 1) / (double)g.decay_steps);
+            a.g[i].lr = (float)((double)g.lr * std::pow((double)g.lr_end / (double)g.lr, f));
+        }
         a.pre[i + 1] = a.pre[i] + (g.n + 3) / 4;
-        a.vec[i] = g.stride == 1 && al16(g.param) && al16(g.grad) && al16(g.m) && al16(g.v);
+        a.vec[i] = g.stride == 1 && g.zero_lead == 0 && al16(g.param) && al16(g.grad) && al16(g.m) && al16(g.v);
     }
     a.b1 = b1;
     a.b2 = b2;

@@ -852,6 +852,10 @@ rogs_status rogs_adam_step(rogs_ctx* ctx, const rogs_adam_group* groups, int32_t
     for (int i = 0; i < n_groups; ++i) {
         const rogs_adam_group& g = groups[i];
         if (g.n < 0 || g.stride < 1) return fail(ctx, ROGS_ERR_INVALID, "group with n < 0 or stride < 1");
+        if (g.zero_lead < 0 || g.zero_lead >= g.stride)
+            return fail(ctx, ROGS_ERR_INVALID, "group with zero_lead outside [0, stride)");
+        if (g.decay_steps < 0 || (g.decay_steps > 0 && !(g.lr > 0.0f && g.lr_end > 0.0f)))
+            return fail(ctx, ROGS_ERR_INVALID, "group with decay_steps < 0, or a decay without positive lr and lr_end");
         if (g.n > 0 && (!g.param || !g.grad || !g.m || !g.v)) return fail(ctx, ROGS_ERR_INVALID, "null group pointer");
     }
     adam_step(groups, n_groups, step, beta1, beta2, eps, zero_grad != 0, (cudaStream_t)stream);

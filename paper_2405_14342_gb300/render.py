@@ -279,37 +279,37 @@ def render(renderer: Renderer, cams, xyz, scale, quat, opacity, rgb, sem, exposu
     return RenderFunction.apply(renderer, frame, xyz, scale, quat, opacity, rgb, sem, exposure), frame
 
 
-# Sec. 4.2 learning rates (z: proportional to the scene size, see z_lr)
+# Sec. 4.2 learning rates; z's rate is Z_LR_RANGE times the scene size,
+# falling from the first value to the second over the training steps
 PAPER_LR = {"opacity": 1e-4, "scale": 1e-4, "quat": 1e-4, "rgb": 0.008, "sem": 0.1, "exposure": 0.001}
-
-
-def z_lr(step, total_steps, scene_size, start=1.6e-4, end=1.6e-6):
-    """z learning rate: scene size x a ratio falling from 1.6e-4 to 1.6e-6
-    (log-linear in the step; the paper gives only the two ends)."""
-    f = min(max(step / max(total_steps, 1), 0.0), 1.0)
-    return scene_size * start * (end / start) ** f
+Z_LR_RANGE = (1.6e-4, 1.6e-6)
 
 
 class Adam:
     """Adam state (m, v) for a SurfelTensors + exposure tensor and one fused
-    step over all of them (rogs_adam_step): z only of the positions, then
+    step over all of them (rogs_adam_step): z only of the positions (its rate
+    decays inside the library from scene_size x 1.6e-4 to scene_size x 1.6e-6
+    over total_steps; x and y gradients are cleared, not learnt), then
     opacity, scale, quat, rgb, sem, exposure with the paper's rates."""
 
-    def __init__(self, renderer, m: SurfelTensors, exposure: torch.Tensor, lr=None):
+    def __init__(self, renderer, m: SurfelTensors, exposure: torch.Tensor, scene_size: float, total_steps: int,
+                 lr=None):
         self.r, self.m, self.exposure = renderer, m, exposure
         self.lr = dict(PAPER_LR if lr is None else lr)
+        self.scene_size, self.total_steps = float(scene_size), int(total_steps)
         self.t = 0
         sizes = {"z": m.n, "opacity": m.opacity.numel(), "scale": m.scale.numel(), "quat": m.quat.numel(),
                  "rgb": m.rgb.numel(), "sem": m.sem.numel(), "exposure": exposure.numel()}
         self.state = {k: (torch.zeros(n, device=m.xyz.device), torch.zeros(n, device=m.xyz.device))
                       for k, n in sizes.items()}
 
-    def step(self, grads: dict, z_lr_now: float, zero_grad=True, stream=None):
+    def step(self, grads: dict, zero_grad=True, stream=None):
         self.t += 1
         m = self.m
         groups = []
         mv = self.state
-        groups.append((m.xyz[:, 2], grads["xyz"][:, 2], *mv["z"], m.n, 3, z_lr_now))
+        z0, z1 = (self.scene_size * r for r in Z_LR_RANGE)
+        groups.append((m.xyz[:, 2], grads["xyz"][:, 2], *mv["z"], m.n, 3, z0, z1, self.total_steps, 2))
         for k in ("opacity", "scale", "quat", "rgb", "sem"):
             p = getattr(m, k)
             if p.numel():
@@ -317,5 +317,3 @@ class Adam:
         groups.append((self.exposure, grads["exposure"], *mv["exposure"], self.exposure.numel(), 1,
                        self.lr["exposure"]))
         R.rogs_adam_step(self.r.ctx, groups, self.t, zero_grad=zero_grad, stream=stream)
-        if zero_grad:   # x and y are not learnt (Sec. 4.2): their gradient is dropped
-            grads["xyz"][:, :2].zero_()

@@ -52,7 +52,8 @@ class rogs_surfels(C.Structure):
 
 class rogs_adam_group(C.Structure):
     _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p), ("v", C.c_void_p),
-                ("n", C.c_int64), ("stride", C.c_int32), ("lr", C.c_float)]
+                ("n", C.c_int64), ("stride", C.c_int32), ("lr", C.c_float), ("lr_end", C.c_float),
+                ("decay_steps", C.c_int32), ("zero_lead", C.c_int32)]
 
 
 ROGS_MAX_ADAM_GROUPS = 16
@@ -309,13 +310,17 @@ def rogs_bev_export(ctx, surf: rogs_surfels, exposure_ab, exposure_idx, x0, y1, 
 
 
 def rogs_adam_step(ctx, groups, step, beta1=0.9, beta2=0.999, eps=1e-8, zero_grad=True, stream=None):
-    """groups: list of (param, grad, m, v, n, stride, lr) with device tensors
-    (param / grad may be views offset into a larger tensor)."""
+    """groups: list of (param, grad, m, v, n, stride, lr) or (param, grad, m, v,
+    n, stride, lr, lr_end, decay_steps, zero_lead) with device tensors (param /
+    grad may be views offset into a larger tensor)."""
     arr = (rogs_adam_group * len(groups))()
-    for i, (p, g, m, v, n, stride, lr) in enumerate(groups):
+    for i, grp in enumerate(groups):
+        p, g, m, v, n, stride, lr = grp[:7]
+        lr_end, decay, lead = grp[7:10] if len(grp) > 7 else (lr, 0, 0)
         arr[i].param, arr[i].grad = p.data_ptr(), g.data_ptr()
         arr[i].m, arr[i].v = m.data_ptr(), v.data_ptr()
         arr[i].n, arr[i].stride, arr[i].lr = int(n), int(stride), float(lr)
+        arr[i].lr_end, arr[i].decay_steps, arr[i].zero_lead = float(lr_end), int(decay), int(lead)
     _check(ctx, lib().rogs_adam_step(ctx, arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
                                      1 if zero_grad else 0, _stream(stream)))
 

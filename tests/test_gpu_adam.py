@@ -24,7 +24,7 @@ def test_adam_groups_match_oracle(R):
     rr = R.Renderer(5, record_capacity=1 << 12, pair_capacity=1 << 12)
     st = R.SurfelTensors.from_map(m)
     ex = torch.as_tensor(rng.normal(0, 0.1, (3, 2)).astype(np.float32), device="cuda")
-    opt = R.Adam(rr, st, ex)
+    opt = R.Adam(rr, st, ex, scene_size=5.0, total_steps=10)
     ref = {"z": m.xyz[:, 2].astype(np.float64), "scale": m.scale.ravel().astype(np.float64),
            "quat": m.quat.ravel().astype(np.float64), "opacity": m.opacity.astype(np.float64),
            "rgb": m.rgb.ravel().astype(np.float64), "sem": m.sem.ravel().astype(np.float64),
@@ -38,8 +38,8 @@ def test_adam_groups_match_oracle(R):
             gv = rng.normal(0, 1e-2, tuple(g.shape)).astype(np.float32)
             g.copy_(torch.as_tensor(gv))
             gnp[k] = gv
-        zl = R.z_lr(t, 10, 5.0)
-        opt.step(grads, zl)
+        zl = oracle.z_learning_rate(t - 1, 10, 5.0)   # the schedule runs inside rogs_adam_step
+        opt.step(grads)
         torch.cuda.synchronize()
         gmap = {"z": gnp["xyz"][:, 2], "scale": gnp["scale"].ravel(), "quat": gnp["quat"].ravel(),
                 "opacity": gnp["opacity"], "rgb": gnp["rgb"].ravel(), "sem": gnp["sem"].ravel(),
@@ -57,6 +57,34 @@ def test_adam_groups_match_oracle(R):
         lr = R.PAPER_LR.get(k, 5.0 * 1.6e-4)
         assert np.abs(a - ref[k]).max() <= 1e-6 * max(1.0, np.abs(ref[k]).max()) + 1e-4 * lr, k
     assert torch.equal(st.xyz[:, :2], xy0)          # x, y are not learnt
+
+
+def test_z_rate_schedule_and_xy_clearing(R):
+    """The z column's rate follows the log-linear decay inside the library and
+    stays at its end value after decay_steps; the x and y gradients are cleared
+    with the z gradient (x, y are not learnt), other columns are untouched."""
+    from paper_2405_14342_gb300 import rogs
+    rr = R.Renderer(2, record_capacity=1 << 12, pair_capacity=1 << 12)
+    n = 1000
+    xyz = torch.zeros(n, 3, device="cuda")
+    g = torch.zeros(n, 3, device="cuda")
+    mm, vv = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    lr0, lr1, D = 0.5, 0.005, 4
+    for t in range(1, 8):
+        g.fill_(1.0)
+        z_before = xyz[:, 2].clone()
+        rogs.rogs_adam_step(rr.ctx, [(xyz[:, 2], g[:, 2], mm, vv, n, 3, lr0, lr1, D, 2)], t)
+        torch.cuda.synchronize()
+        # with a constant gradient of 1 the bias-corrected Adam update is lr_t / (1 + eps)
+        step = (z_before - xyz[:, 2]).cpu().numpy().astype(np.float64)
+        lr_t = oracle.z_learning_rate(t - 1, D, 1.0, start=lr0, end=lr1)
+        assert np.abs(step - lr_t).max() < 1e-5 * lr_t + 1e-7, (t, step[:3], lr_t)
+        assert not g.any()
+        assert not xyz[:, :2].any()
+    with pytest.raises(rogs.RogsError):   # zero_lead must stay inside the stride
+        rogs.rogs_adam_step(rr.ctx, [(xyz[:, 2], g[:, 2], mm, vv, n, 3, lr0, lr1, D, 3)], 1)
+    with pytest.raises(rogs.RogsError):   # a decay needs positive ends
+        rogs.rogs_adam_step(rr.ctx, [(xyz[:, 2], g[:, 2], mm, vv, n, 3, lr0, 0.0, D, 0)], 1)
 
 
 def test_adam_rejects_bad_arguments(R):
@@ -94,7 +122,7 @@ def test_optimisation_reduces_the_loss(R):
     m2 = m.copy()
     m2.rgb = np.clip(m2.rgb + rng.normal(0, 0.2, m2.rgb.shape), 0, 1).astype(np.float32)
     st = R.SurfelTensors.from_map(m2, grid_index=gi)
-    opt = R.Adam(rr, st, ex, lr=dict(R.PAPER_LR, rgb=0.02))
+    opt = R.Adam(rr, st, ex, scene_size=6.4, total_steps=30, lr=dict(R.PAPER_LR, rgb=0.02))
     grads = R.zero_grads(st, ex)
     fr = rr.frame(cams)
     loss = torch.empty(1, device="cuda")
@@ -102,6 +130,6 @@ def test_optimisation_reduces_the_loss(R):
     for t in range(30):
         rr.train_step(st, fr, ex, trgb, lab, msk, loss, grads, lambda_smooth=0.003)
         losses.append(float(loss.item()))
-        opt.step(grads, R.z_lr(t, 30, 6.4))
+        opt.step(grads)
     torch.cuda.synchronize()
     assert losses[-1] < 0.7 * losses[0], losses
