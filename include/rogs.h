@@ -163,9 +163,21 @@ void rogs_destroy(rogs_ctx* ctx);
 /* Last error message of this context ("" if none).  Valid until the next call. */
 const char* rogs_last_error(const rogs_ctx* ctx);
 
-/* Pre-size scratch for maps of up to n_surfels and up to n_views views so
-   that later calls (e.g. inside CUDA-graph capture) never allocate. */
-rogs_status rogs_reserve(rogs_ctx* ctx, int64_t n_surfels, int32_t n_views);
+/* Pre-size scratch so that later calls never allocate, synchronise or free
+   (as CUDA-graph capture requires): the visibility scratch for maps of up to
+   n_surfels surfels and up to n_views views; and, when `training` is nonzero,
+   also the per-record gradient rows of the backward (record_capacity rows,
+   cleared here) and, when `cams` (host, n_views entries) is given, the loss
+   scratch for calls over those cameras (or any camera set with no more
+   pixels and tiles).  After a matching reserve, rogs_render_fwd, rogs_loss,
+   rogs_render_bwd and rogs_train_step only enqueue kernels and asynchronous
+   copies on their stream.  Without it, the first call that needs more
+   scratch grows it: that call synchronises its stream, frees the old buffer
+   and allocates (and is refused with ROGS_ERR_CAPACITY during a capture).
+   Synchronises the device.  Errors: ROGS_ERR_INVALID for n_surfels < 0 or
+   n_views outside [1, ROGS_MAX_VIEWS] or a bad camera; ROGS_ERR_OOM. */
+rogs_status rogs_reserve(rogs_ctx* ctx, int64_t n_surfels, const rogs_camera* cams, int32_t n_views,
+                         int32_t training);
 
 /* Output and state geometry of a set of cameras (host-side arithmetic).
    out_elems = (3 + C + 1) * total pixels floats: view v occupies
@@ -421,6 +433,10 @@ rogs_status rogs_serve_poll(rogs_server* srv, uint64_t ticket, void* host_out, i
 
 rogs_status rogs_serve_get_stats(rogs_server* srv, rogs_serve_stats* out);
 
+/* Change the server's timeout_s (thread-safe; > 0).  Batches already in
+   flight are judged against the new value from the next check on. */
+rogs_status rogs_serve_set_timeout(rogs_server* srv, double timeout_s);
+
 /* Stop the worker, wait (bounded by timeout_s) for batches in flight, free
    everything.  Unpolled results are dropped. */
 void rogs_serve_close(rogs_server* srv);
@@ -504,8 +520,24 @@ rogs_status rogs_profile_enable(rogs_ctx* ctx, int32_t enable);
 /* Wait for the recorded events and return the totals since the last enable. */
 rogs_status rogs_profile_read(rogs_ctx* ctx, rogs_profile* out);
 
+/* Measure the current device's FP32 fused multiply-add rate (a measurement
+   utility, not part of the method): a kernel of independent FMA chains on
+   every SM, timed with CUDA events on `stream`, best of `reps` launches after
+   one warm-up; *tflops = 2 x FMAs / time in TFLOP/s, *sm_count (optional) =
+   the device's SM count.  Allocates and frees a small buffer and
+   synchronises the stream.  Errors: ROGS_ERR_INVALID (reps < 1, NULL
+   tflops), ROGS_ERR_OOM, ROGS_ERR_CUDA. */
+rogs_status rogs_measure_fp32_peak(int32_t reps, double* tflops, int32_t* sm_count, rogs_stream stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t rogs_launch_count(void);
+
+/* Test hook for failure handling (the paper has no counterpart): while
+   fail_all is nonzero, every device allocation the library makes for its own
+   scratch (rogs_create, rogs_reserve, growth inside a call, the serving
+   pool) reports out-of-memory, so callers can check that ROGS_ERR_OOM comes
+   back cleanly and that nothing leaks.  Process-wide; not for production. */
+void rogs_debug_fail_alloc(int32_t fail_all);
 
 #ifdef __cplusplus
 }

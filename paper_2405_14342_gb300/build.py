@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build", "librogs")
 LIB = os.path.join(HERE, "librogs.so")
 SOURCES = ["api.cu", "project.cu", "sort.cu", "bin.cu", "composite.cu", "backward.cu", "loss.cu", "init.cu",
-           "noalloc.cu", "serve.cu", "smooth.cu", "adam.cu", "lidar.cu", "bev.cu"]
+           "noalloc.cu", "serve.cu", "smooth.cu", "adam.cu", "lidar.cu", "bev.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

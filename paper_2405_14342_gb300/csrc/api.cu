@@ -22,6 +22,10 @@ using namespace rogs;
 namespace rogs {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+// Test hook (rogs_debug_fail_alloc): while set, every scratch allocation of
+// the library reports that the device is out of memory.
+static std::atomic<int> g_fail_alloc{0};
+bool debug_alloc_fails() { return g_fail_alloc.load() != 0; }
 }  // namespace rogs
 
 struct rogs_graph {
@@ -136,9 +140,15 @@ rogs_status grow(rogs_ctx* ctx, T*& ptr, size_t& cap, size_t need, cudaStream_t 
         cap = 0;
     }
     size_t n = need > 0 ? need : 1;
-    cudaError_t e = cudaMalloc((void**)&ptr, n * sizeof(T));
-    if (e != cudaSuccess) return fail(ctx, ROGS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    if (zero) cudaMemset(ptr, 0, n * sizeof(T));
+    cudaError_t e = debug_alloc_fails() ? cudaErrorMemoryAllocation : cudaMalloc((void**)&ptr, n * sizeof(T));
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        return fail(ctx, ROGS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    // cleared on the stream of the call that grew it, so the clear is ordered
+    // before that call's kernels
+    if (zero && cudaMemsetAsync(ptr, 0, n * sizeof(T), s) != cudaSuccess)
+        return fail(ctx, ROGS_ERR_CUDA, "cudaMemsetAsync of new scratch failed");
     cap = n;
     return ROGS_OK;
 }
@@ -424,10 +434,23 @@ static rogs_status ensure_loss(rogs_ctx* ctx, long long total_pix, cudaStream_t 
     return st;
 }
 
-rogs_status rogs_reserve(rogs_ctx* ctx, int64_t n_surfels, int32_t n_views) {
+rogs_status rogs_reserve(rogs_ctx* ctx, int64_t n_surfels, const rogs_camera* cams, int32_t n_views,
+                         int32_t training) {
     if (!ctx || n_surfels < 0 || n_views < 1 || n_views > kMaxViews) return fail(ctx, ROGS_ERR_INVALID, "bad reserve");
-    return ensure_bits(ctx, n_surfels, n_views, nullptr);
+    rogs_status st = ensure_bits(ctx, n_surfels, n_views, nullptr);
+    if (st == ROGS_OK && training) st = ensure_rec_grad(ctx, nullptr);
+    if (st == ROGS_OK && training && cams) {
+        static thread_local ViewsArg va;
+        long long tt, tp;
+        std::string err;
+        if (!make_views(ctx->cfg, cams, n_views, va, tt, tp, err)) return fail(ctx, ROGS_ERR_INVALID, err);
+        st = ensure_loss(ctx, tp, nullptr, (size_t)bwd_loss_partials(tt, ctx->cfg.tile_w, ctx->cfg.tile_h));
+    }
+    if (st == ROGS_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(ctx, ROGS_ERR_CUDA, "reserve: synchronise");
+    return st;
 }
+
+void rogs_debug_fail_alloc(int32_t fail_all) { g_fail_alloc.store(fail_all ? 1 : 0); }
 
 rogs_status rogs_state_layout_of(const rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views,
                                  rogs_state_layout* layout, uint64_t* out_elems) {

@@ -13,6 +13,8 @@ namespace rogs {
 
 // Count kernel launches made by this library (reported by rogs_launch_count).
 void note_launches(int n);
+// True while the rogs_debug_fail_alloc test hook makes scratch allocations fail.
+bool debug_alloc_fails();
 
 struct SurfelPtrs {
     const float *xyz, *scale, *quat, *opacity, *rgb, *sem;

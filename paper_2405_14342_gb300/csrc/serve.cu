@@ -433,7 +433,7 @@ rogs_status rogs_serve_open(const rogs_config* cfg_render, const rogs_surfels* m
         st = rogs_create(&srv->rcfg, &c);
         if (st == ROGS_OK) {
             srv->ctxs.push_back(c);
-            st = rogs_reserve(c, map->n, cfg->max_batch_views);
+            st = rogs_reserve(c, map->n, nullptr, cfg->max_batch_views, 0);
         }
         cudaStream_t s = nullptr;
         if (st == ROGS_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = ROGS_ERR_CUDA;
@@ -442,7 +442,8 @@ rogs_status rogs_serve_open(const rogs_config* cfg_render, const rogs_surfels* m
             srv->slot_busy.push_back(false);
         }
     }
-    if (st == ROGS_OK && cudaMalloc((void**)&srv->pool, cfg->memory_budget) != cudaSuccess) st = ROGS_ERR_OOM;
+    if (st == ROGS_OK && (rogs::debug_alloc_fails() || cudaMalloc((void**)&srv->pool, cfg->memory_budget) != cudaSuccess))
+        st = ROGS_ERR_OOM;
     const size_t pin_size = cfg->memory_budget / 4 + (1u << 20);
     if (st == ROGS_OK && cudaHostAlloc((void**)&srv->pinned, pin_size, cudaHostAllocDefault) != cudaSuccess)
         st = ROGS_ERR_OOM;
@@ -511,6 +512,13 @@ rogs_status rogs_serve_get_stats(rogs_server* srv, rogs_serve_stats* out) {
     if (!srv || !out) return ROGS_ERR_INVALID;
     std::lock_guard<std::mutex> lk(srv->mu);
     *out = srv->stats;
+    return ROGS_OK;
+}
+
+rogs_status rogs_serve_set_timeout(rogs_server* srv, double timeout_s) {
+    if (!srv || !(timeout_s > 0)) return ROGS_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->cfg.timeout_s = timeout_s;
     return ROGS_OK;
 }
 

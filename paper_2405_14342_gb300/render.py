@@ -58,6 +58,7 @@ class Frame:
     out: torch.Tensor       # float[(3+C+1) * total_pixels]
     state: torch.Tensor     # uint8[layout.total_bytes]
     pix_base: List[int]
+    generation: int = 0     # forwards run on this frame (its state belongs to the latest)
 
     def view(self, v: int, C: int) -> torch.Tensor:
         """Planes [3+C+1, H, W] of view v."""
@@ -105,8 +106,14 @@ class Renderer:
     def nch(self) -> int:
         return 3 + self.C + 1
 
-    def reserve(self, n_surfels: int, n_views: int):
-        R.rogs_reserve(self.ctx, n_surfels, n_views)
+    def reserve(self, n_surfels: int, n_views: int = None, cams: Sequence = None, training: bool = False):
+        """Size the context's scratch up front (rogs_reserve): for n_surfels and
+        n_views (or len(cams)); with training, also the backward's gradient rows
+        and, given cams, the loss scratch for frames of those cameras.  Later
+        calls then never allocate or synchronise (graph capture needs this)."""
+        arr = R.cameras(cams) if cams is not None else None
+        nv = len(cams) if cams is not None else int(n_views)
+        R.rogs_reserve(self.ctx, n_surfels, nv, arr, training)
 
     def frame(self, cams: Sequence) -> Frame:
         arr = R.cameras(cams)
@@ -122,6 +129,7 @@ class Renderer:
     # -- the C-ABI calls --------------------------------------------------
 
     def forward(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, stream=None) -> Frame:
+        frame.generation += 1
         R.rogs_render_fwd(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
                           frame.state, stream)
         return frame
@@ -159,6 +167,7 @@ class Renderer:
         """Forward, masked L1 + CE loss and backward with the loss fused into the
         backward kernel (rogs_train_step), plus lambda_smooth L_smooth when
         nonzero; gradients are added into `grads`."""
+        frame.generation += 1
         R.rogs_train_step(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out, frame.state,
                           tgt_rgb, label, mask, lambda_c, lambda_s, loss, self.grads_struct(grads), stream,
                           lambda_smooth)
@@ -258,23 +267,38 @@ def targets_to_device(targets, device="cuda"):
 
 
 class RenderFunction(torch.autograd.Function):
-    """out = render(surfels, exposure); backward via rogs_render_bwd."""
+    """out = render(surfels, exposure); backward via rogs_render_bwd.
+
+    The compositing state the backward recomputes from (records, tile lists,
+    final transmittance and last contributor per pixel) lives in the frame, so
+    the backward refuses to run if the frame was rendered again after this
+    forward (its state would belong to the later forward).  The backward runs
+    on the stream autograd gives it, after the forward's stream."""
 
     @staticmethod
     def forward(ctx, renderer: Renderer, frame: Frame, xyz, scale, quat, opacity, rgb, sem, exposure):
         m = SurfelTensors(xyz.detach(), scale.detach(), quat.detach(), opacity.detach(), rgb.detach(), sem.detach())
-        renderer.forward(m, frame, exposure.detach())
+        stream = torch.cuda.current_stream(frame.out.device)
+        renderer.forward(m, frame, exposure.detach(), stream)
         ctx.renderer, ctx.frame, ctx.m, ctx.exposure = renderer, frame, m, exposure.detach()
+        ctx.generation, ctx.stream = frame.generation, stream
         return frame.out.clone()
 
     @staticmethod
     def backward(ctx, grad_out):
-        g = ctx.renderer.backward(ctx.m, ctx.frame, ctx.exposure, grad_out.contiguous())
+        if ctx.frame.generation != ctx.generation:
+            raise RuntimeError("the frame was rendered again after this forward; render each graph's forward into "
+                               "its own frame (render(..., frame=None)) before calling backward")
+        stream = torch.cuda.current_stream(grad_out.device)
+        if stream != ctx.stream:
+            stream.wait_stream(ctx.stream)
+        g = ctx.renderer.backward(ctx.m, ctx.frame, ctx.exposure, grad_out.contiguous(), stream=stream)
         return (None, None, g["xyz"], g["scale"], g["quat"], g["opacity"], g["rgb"], g["sem"], g["exposure"])
 
 
 def render(renderer: Renderer, cams, xyz, scale, quat, opacity, rgb, sem, exposure, frame: Frame = None):
-    """Differentiable render of `cams`; returns the flat output planes."""
+    """Differentiable render of `cams`; returns the flat output planes (view v
+    at [(3+C+1) pix_base[v], ...), planes rgb, C logits, depth) and the frame."""
     frame = renderer.frame(cams) if frame is None else frame
     return RenderFunction.apply(renderer, frame, xyz, scale, quat, opacity, rgb, sem, exposure), frame
 

@@ -120,7 +120,7 @@ def lib():
         L.rogs_destroy.restype = None
         L.rogs_last_error.argtypes = [P]
         L.rogs_last_error.restype = C.c_char_p
-        L.rogs_reserve.argtypes = [P, C.c_int64, C.c_int32]
+        L.rogs_reserve.argtypes = [P, C.c_int64, C.POINTER(rogs_camera), C.c_int32, C.c_int32]
         L.rogs_state_layout_of.argtypes = [P, C.POINTER(rogs_camera), C.c_int32, C.POINTER(rogs_state_layout),
                                            C.POINTER(C.c_uint64)]
         L.rogs_state_counts.argtypes = [P, P, C.POINTER(rogs_counts), P]
@@ -154,15 +154,19 @@ def lib():
         L.rogs_serve_submit.argtypes = [P, C.POINTER(rogs_camera), C.c_int32, C.POINTER(C.c_uint64)]
         L.rogs_serve_poll.argtypes = [P, C.c_uint64, P, C.POINTER(C.c_int32)]
         L.rogs_serve_get_stats.argtypes = [P, C.POINTER(rogs_serve_stats)]
+        L.rogs_serve_set_timeout.argtypes = [P, C.c_double]
+        L.rogs_debug_fail_alloc.argtypes = [C.c_int32]
+        L.rogs_debug_fail_alloc.restype = None
         L.rogs_serve_close.argtypes = [P]
         L.rogs_serve_close.restype = None
         L.rogs_profile_enable.argtypes = [P, C.c_int32]
         L.rogs_profile_read.argtypes = [P, C.POINTER(rogs_profile)]
+        L.rogs_measure_fp32_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32), P]
         L.rogs_launch_count.argtypes = []
         L.rogs_launch_count.restype = C.c_uint64
         for name in ("rogs_train_step", "rogs_smooth_loss", "rogs_adam_step", "rogs_elev_targets", "rogs_elev_loss", "rogs_bev_export",
                      "rogs_serve_result_bytes", "rogs_serve_open", "rogs_serve_submit", "rogs_serve_poll",
-                     "rogs_serve_get_stats", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
+                     "rogs_serve_get_stats", "rogs_serve_set_timeout", "rogs_measure_fp32_peak", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
                      "rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
                      "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
                      "rogs_render_bwd", "rogs_sort_pairs"):
@@ -242,8 +246,19 @@ def rogs_last_error(ctx) -> str:
     return lib().rogs_last_error(ctx).decode()
 
 
-def rogs_reserve(ctx, n_surfels, n_views):
-    _check(ctx, lib().rogs_reserve(ctx, int(n_surfels), int(n_views)))
+def rogs_reserve(ctx, n_surfels, n_views, cam_arr=None, training=False):
+    _check(ctx, lib().rogs_reserve(ctx, int(n_surfels), cam_arr, int(n_views), 1 if training else 0))
+
+
+def rogs_measure_fp32_peak(reps=5, stream=None):
+    """(measured FP32 FMA TFLOP/s, SM count) of the current device."""
+    t, n = C.c_double(), C.c_int32()
+    _check(None, lib().rogs_measure_fp32_peak(int(reps), C.byref(t), C.byref(n), _stream(stream)))
+    return float(t.value), int(n.value)
+
+
+def rogs_debug_fail_alloc(fail_all: bool):
+    lib().rogs_debug_fail_alloc(1 if fail_all else 0)
 
 
 def rogs_state_layout_of(ctx, cam_arr, n_views):
@@ -414,6 +429,10 @@ def rogs_serve_get_stats(srv) -> rogs_serve_stats:
     s = rogs_serve_stats()
     _check(None, lib().rogs_serve_get_stats(srv, C.byref(s)))
     return s
+
+
+def rogs_serve_set_timeout(srv, timeout_s):
+    _check(None, lib().rogs_serve_set_timeout(srv, float(timeout_s)))
 
 
 def rogs_serve_close(srv):

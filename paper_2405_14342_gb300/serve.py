@@ -56,6 +56,9 @@ class Server:
                 raise TimeoutError(f"request {ticket} not finished after {timeout} s")
             time.sleep(sleep)
 
+    def set_timeout(self, timeout_s: float):
+        R.rogs_serve_set_timeout(self.h, timeout_s)
+
     def stats(self) -> R.rogs_serve_stats:
         return R.rogs_serve_get_stats(self.h)
 

@@ -74,3 +74,19 @@ def normwise(a, b):
     if m == 0.0:
         return float(np.abs(a).max()) if a.size else 0.0
     return float(np.abs(a - b).max() / m)
+
+
+def elementwise(a, b, rtol=1e-3, floor=1e-6):
+    """Element-wise gradient check of the benchmark spec's tolerance with a floor:
+    |a - b| <= rtol * max(|b|, floor * max|b|).  Returns the number of entries,
+    the entries outside the bound (indices), and the worst ratio
+    |a - b| / (rtol * max(|b|, floor * max|b|))."""
+    a = np.asarray(a, np.float64).ravel(); b = np.asarray(b, np.float64).ravel()
+    if b.size == 0:
+        return 0, np.zeros(0, np.int64), 0.0
+    m = np.abs(b).max()
+    bound = rtol * np.maximum(np.abs(b), floor * m)
+    err = np.abs(a - b)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = np.where(bound > 0, err / bound, np.where(err > 0, np.inf, 0.0))
+    return b.size, np.nonzero(ratio > 1.0)[0], float(ratio.max())

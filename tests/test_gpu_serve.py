@@ -139,3 +139,31 @@ def test_admission_errors(env):
             srv.poll(tickets[0]) if tickets[0] in srv._meta else rogs.rogs_serve_poll(srv.h, tickets[0], None)
     finally:
         srv.close()
+
+
+def test_serve_timeout_is_reported_and_the_server_keeps_serving(env):
+    """A batch still running after timeout_s fails its requests with
+    ROGS_ERR_TIMEOUT (the host stops waiting; the GPU work itself finishes and
+    its memory is released then); with a longer timeout the same server then
+    serves new requests correctly."""
+    rogs = env["rogs"]
+    srv = env["serve"].Server(env["cfg"], env["st"], env["ex"], max_batch_views=1, max_inflight=1,
+                              memory_budget=4 << 30, record_capacity=1 << 18, pair_capacity=1 << 23,
+                              timeout_s=1e-6)
+    try:
+        big = scenes.bev_camera((3.1, 3.1), 4096, res_m=0.002, height_m=30.0)   # 16.8 Mpx, 285 MB of result
+        t = srv.submit(big, 7)
+        with pytest.raises(rogs.RogsError) as ei:
+            srv.wait(t, timeout=60.0)
+        assert ei.value.status == rogs.ROGS_ERR_TIMEOUT
+        assert srv.stats().failed == 1
+        srv.set_timeout(30.0)
+        cam, ch = requests()[1]
+        r = srv.wait(srv.submit(cam, ch))
+    finally:
+        srv.close()
+    pix = oracle.full_pixels([cam])
+    ref = oracle.render(env["m"], [cam], env["ex_np"], pix)
+    ok = (ref.amb == 0).reshape(cam.height, cam.width)
+    out = ref.out.reshape(cam.height, cam.width, -1)
+    assert np.abs(r["rgb"].transpose(1, 2, 0)[ok] - out[ok][:, :3]).max() < 1e-4
