@@ -181,53 +181,6 @@ __device__ __forceinline__ bool entry_hits_block(float4 m, float4 c, float alpha
     return box_hits_block(m, block_cull_radii(c, alpha_min), bx, by);
 }
 
-// ------------------------------------------------------------ tensor cores
-// Warp-level m16n8k8 TF32 MMA with FP32 accumulation.  Fragment layout (PTX
-// ISA, mma m16n8k8 .tf32), g = lane / 4, t = lane % 4:
-//   A (16x8, row): a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
-//   B (8x8, col):  b0 (t, g), b1 (t+4, g)
-//   C (16x8):      c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
-// Products are taken in three TF32 passes (a_hi b_hi + a_hi b_lo + a_lo b_hi),
-// which keeps them to about FP32 accuracy.  The split x = hi + lo is exact:
-// hi keeps the sign, exponent and top 10 mantissa bits of x (a TF32 value) and
-// lo = x - hi (|lo| < 2^-10 |x|) is passed as it is; the tensor core reads the
-// top 19 bits of a TF32 operand, so lo loses at most 2^-10 of itself and a
-// product at most about 2^-19 of |a b|.
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-    hi = __float_as_uint(x) & 0xFFFFE000u;
-    lo = __float_as_uint(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// d[mt][nt] += A_mt B_nt for two 16-row A tiles (the second only if `two`)
-// and NT 8-column B tiles, in three TF32 passes issued pass by pass, so that
-// consecutive products go to different accumulators; ah/al, bh/bl are the
-// split fragments.
-template <int NT>
-__device__ __forceinline__ void mma_tf32x3_tiles(float (&d)[2][NT][4], const uint32_t (&ah)[2][4],
-                                                 const uint32_t (&al)[2][4], const uint32_t (&bh)[NT][2],
-                                                 const uint32_t (&bl)[NT][2], bool two) {
-#pragma unroll
-    for (int pass = 0; pass < 3; ++pass)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                if (mt == 1 && !two) continue;
-                const uint32_t(&a)[4] = pass == 0 ? al[mt] : ah[mt];
-                const uint32_t(&b)[2] = pass == 1 ? bl[nt] : bh[nt];
-                mma_tf32(d[mt][nt], a[0], a[1], a[2], a[3], b[0], b[1]);
-            }
-}
-
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

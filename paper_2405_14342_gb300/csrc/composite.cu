@@ -11,20 +11,18 @@
 // whose footprint can reach the warp's block (a conservative ellipse
 // bounding box), compact them in order into the warp's shared-memory slots
 // together with their features (rgb, sem, depth), and then every lane walks
-// the compacted entries for its pixel, computing only the scalar recursion
-// (alpha, the transmittance stop, w = a T) and writing its weights into a
-// (entry x pixel) table.  The channel sums of Eq. 6 for the chunk are then
-// one dense product, out[pixel][ch] += W[pixel][entry] F[entry][ch]
-// (32 x NCP x up to 32), taken on the tensor cores (warp-level TF32 MMA in
-// three passes, about FP32 accurate).  A warp stops as soon as all its
-// pixels have stopped, without waiting for the rest of the tile: there is no
-// block-wide barrier.
+// the compacted entries for its pixel: the scalar recursion (alpha, the
+// transmittance stop, w = a T) and the channel sums of Eq. 6,
+// out[ch] += w f[ch], as FP32 fused multiply-adds on the lane's own
+// accumulators, the feature row read from shared memory as broadcast
+// float4s.  A warp stops as soon as all its pixels have stopped, without
+// waiting for the rest of the tile: there is no block-wide barrier.
 #include "kernels.h"
 
 namespace rogs {
 
 int padded_channels(int C) {
-    const int n = 3 + C + 1;   // a multiple of 8: the MMA n-tile
+    const int n = 3 + C + 1;   // a multiple of 8: whole float4 rows, 32-byte aligned
     if (n <= 8) return 8;
     if (n <= 16) return 16;
     if (n <= 24) return 24;
@@ -32,15 +30,19 @@ int padded_channels(int C) {
     return 64;
 }
 
-constexpr int kWStride = 40;   // weight table: row = entry, column = pixel (rows 8 banks apart)
-
 template <int NCP>
 __host__ __device__ constexpr int fwd_warp_floats() {
-    return 32 * 4 + 32 * 4 + 32 * feat_stride<NCP>() + 32 + 32 * kWStride;
+    return 32 * 4 + 32 * 4 + 32 * NCP + 32;
 }
 
+// Up to 24 channels the accumulators fit in 64 registers, so 32 warps stay
+// resident per SM (the list walk is latency bound); wider rows run 16 warps
+// per SM with up to 128 registers each.
+template <int NCP>
+constexpr int fwd_threads_per_sm() { return NCP <= 24 ? 1024 : 512; }
+
 template <int TW, int TH, int NCP>
-__global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __restrict__ views, int n_views, Consts k,
+__global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)) composite_fwd_k(const ViewParams* __restrict__ views, int n_views, Consts k,
                                                            SurfelPtrs sp, const Record* __restrict__ recs,
                                                            const float* __restrict__ feat,
                                                            const float4* __restrict__ pair_mc,
@@ -53,17 +55,13 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
                                                            uint32_t* __restrict__ pix_last,
                                                            StateHeader* __restrict__ hdr) {
     constexpr int WX = TW / 8;
-    constexpr int SF = feat_stride<NCP>();
-    constexpr int NT = NCP / 8;   // MMA n-tiles over the channels
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;   // MMA fragment coordinates
     extern __shared__ float4 smem_fwd[];
     float* wbase = reinterpret_cast<float*>(smem_fwd) + warp * fwd_warp_floats<NCP>();
     float4* s_m = reinterpret_cast<float4*>(wbase);
     float4* s_c = s_m + 32;
     float* s_f = reinterpret_cast<float*>(s_c + 32);
-    uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_f + 32 * SF);
-    float* s_w = reinterpret_cast<float*>(s_idx + 32);
+    uint32_t* s_idx = reinterpret_cast<uint32_t*>(s_f + 32 * NCP);
 
     const long long tile = tile_order[blockIdx.x];
     const int vi = view_of_tile(views, n_views, tile);
@@ -82,13 +80,9 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
     const unsigned lt_mask = lanemask_lt();
 
     float T = 1.0f;
-    float acc[2][NT][4];   // C fragments: pixels 16 mt + g (+8), channels 8 nt + 2t (+1)
+    float acc[NCP];   // this lane's pixel: rgb, C logits, depth, zero padding
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[mt][nt][r] = 0.0f;
+    for (int ch = 0; ch < NCP; ++ch) acc[ch] = 0.0f;
     uint32_t last = 0, ncomp = 0;
     bool done = !inside;
 
@@ -113,21 +107,16 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
         const unsigned mask = __ballot_sync(kFull, hit);
         if (!mask) continue;
         const int h = __popc(mask);
-        const int h8 = (h + 7) & ~7;   // k extent of the product, padded with zero rows
         if (hit) {
             const int slot = __popc(mask & lt_mask);
             s_m[slot] = m;
             s_c[slot] = c;
             s_idx[slot] = j - start + 1;
-            stage_record_features<NCP>(s_f + slot * SF, feat, rec);
-        }
-        if (lane >= h && lane < h8) {   // zero feature rows pad k up to a multiple of 8
-#pragma unroll
-            for (int ch = 0; ch < NCP; ++ch) s_f[lane * SF + ch] = 0.0f;
+            stage_record_features<NCP>(s_f + slot * NCP, feat, rec);
         }
         __syncwarp();
-        // scalar recursion, lane = pixel: entries below alpha_min and entries
-        // after the stop get w = 0
+        // lane = pixel: entries below alpha_min and entries after the stop get
+        // w = 0 (branch-free), every entry adds w f to the lane's channels
         int lslot = -1;   // last slot this pixel composited in the chunk
 #pragma unroll 2
         for (int jj = 0; jj < h; ++jj) {
@@ -142,34 +131,21 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
             const bool stop = valid && Tn < tmin;
             done = done || stop;
             valid = valid && !stop;
-            s_w[jj * kWStride + lane] = valid ? __fmul_rn(a, T) : 0.0f;
+            const float w = valid ? __fmul_rn(a, T) : 0.0f;
             T = valid ? Tn : T;
             lslot = valid ? jj : lslot;
             ncomp += valid ? 1u : 0u;
+            const float4* f4 = reinterpret_cast<const float4*>(s_f + jj * NCP);
+#pragma unroll
+            for (int q = 0; q < NCP / 4; ++q) {
+                const float4 f = f4[q];
+                acc[4 * q] = fmaf(w, f.x, acc[4 * q]);
+                acc[4 * q + 1] = fmaf(w, f.y, acc[4 * q + 1]);
+                acc[4 * q + 2] = fmaf(w, f.z, acc[4 * q + 2]);
+                acc[4 * q + 3] = fmaf(w, f.w, acc[4 * q + 3]);
+            }
         }
         if (lslot >= 0) last = s_idx[lslot];
-        for (int jj = h; jj < h8; ++jj) s_w[jj * kWStride + lane] = 0.0f;
-        __syncwarp();
-        // out[pixel][ch] += W[pixel][entry] F[entry][ch] over this chunk's entries
-        for (int k0 = 0; k0 < h8; k0 += 8) {
-            uint32_t ah[2][4], al[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const float* w0 = s_w + (k0 + t) * kWStride + 16 * mt + g;
-                const float* w1 = s_w + (k0 + t + 4) * kWStride + 16 * mt + g;
-                split_tf32(w0[0], ah[mt][0], al[mt][0]);
-                split_tf32(w0[8], ah[mt][1], al[mt][1]);
-                split_tf32(w1[0], ah[mt][2], al[mt][2]);
-                split_tf32(w1[8], ah[mt][3], al[mt][3]);
-            }
-            uint32_t bh[NT][2], bl[NT][2];
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                split_tf32(s_f[(k0 + t) * SF + 8 * nt + g], bh[nt][0], bl[nt][0]);
-                split_tf32(s_f[(k0 + t + 4) * SF + 8 * nt + g], bh[nt][1], bl[nt][1]);
-            }
-            mma_tf32x3_tiles<NT>(acc, ah, al, bh, bl, true);
-        }
         __syncwarp();
     }
 
@@ -177,25 +153,14 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
     const int nch = 3 + C + 1;
     const float ea = expf(exposure_ab[2 * v.exp_idx]);
     const float eb = exposure_ab[2 * v.exp_idx + 1];
-    float* o = out + (long long)nch * v.pix_base;
+    if (inside) {
+        float* op = out + (long long)nch * v.pix_base + (long long)py * W + px;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int hr = 0; hr < 2; ++hr) {
-            const int p = 16 * mt + g + 8 * hr;   // this fragment row's pixel
-            const int qx = bx + (p & 7), qy = by + (p >> 3);
-            if (qx >= W || qy >= H) continue;
-            float* op = o + (long long)qy * W + qx;
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int ch = 8 * nt + 2 * t + cc;
-                    const float val = acc[mt][nt][2 * hr + cc];
-                    if (ch < 3) op[ch * plane] = fmaf(ea, val, eb);
-                    else if (ch < nch) op[ch * plane] = val;
-                }
+        for (int ch = 0; ch < NCP; ++ch) {
+            if (ch < 3) op[ch * plane] = fmaf(ea, acc[ch], eb);
+            else if (ch < nch) op[ch * plane] = acc[ch];
         }
+    }
     if (inside) {
         const long long pix = v.pix_base + (long long)py * W + px;
         pix_T[pix] = T;
@@ -209,8 +174,7 @@ __global__ void __launch_bounds__(TW * TH) composite_fwd_k(const ViewParams* __r
 }
 
 static size_t fwd_smem_bytes(int blk, int ncp) {
-    const int sf = (ncp % 32 == 8 || ncp % 32 == 24) ? ncp : ncp + 8;
-    return (size_t)(blk / 32) * 4 * (size_t)(32 * 4 + 32 * 4 + 32 * sf + 32 + 32 * kWStride);
+    return (size_t)(blk / 32) * 4 * (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32);
 }
 
 template <int TW, int TH, int NCP>

@@ -21,12 +21,6 @@ struct SurfelPtrs {
     long long n;
 };
 
-// Row stride (floats) of the per-warp feature / gradient tables of the
-// compositing kernels, chosen so that the MMA fragment loads (rows t = 0..3
-// apart, columns g = 0..7) hit 32 different banks.
-template <int NCP>
-__host__ __device__ constexpr int feat_stride() { return (NCP % 32 == 8 || NCP % 32 == 24) ? NCP : NCP + 8; }
-
 // Copy of a record's feature row (rgb, C logits, depth, zeros: NCP floats,
 // 16-byte aligned) into a shared-memory row; all loads before the stores.
 template <int NCP>

@@ -90,3 +90,35 @@ def elementwise(a, b, rtol=1e-3, floor=1e-6):
     with np.errstate(divide="ignore", invalid="ignore"):
         ratio = np.where(bound > 0, err / bound, np.where(err > 0, np.inf, 0.0))
     return b.size, np.nonzero(ratio > 1.0)[0], float(ratio.max())
+
+
+# Element-wise gradient rule.  North star: 1e-3 relative error on the
+# gradients.  Per entry, |g - g_ref| <= 1e-3 max(|g_ref|, FLOOR max|g_ref|).
+# A floor of 1e-6 max|g_ref| would ask for an absolute error of 1e-9 max|g_ref|,
+# some 60x below the binary32 unit roundoff of the tensor's largest entries,
+# which the FP32 kernels cannot resolve for entries that are small because
+# large terms cancel (measured: such entries are off by up to about 1e-7
+# max|g_ref|).  The floor is 3e-4 max|g_ref| (3e-7 max|g_ref| absolute, five
+# binary32 ulps of the largest entry).  Entries that pass at this floor but not
+# at 1e-6 are counted and reported ("left out"); they must stay below
+# LEFT_OUT_MAX of the nonzero entries of every tensor.
+GRAD_RTOL, GRAD_FLOOR, STRICT_FLOOR, LEFT_OUT_MAX = 1e-3, 3e-4, 1e-6, 0.01
+
+
+def check_gradients(got, ref, keys=("xyz", "scale", "quat", "opacity", "rgb", "sem", "exposure")):
+    """Normwise and element-wise checks of gradient tensors (dicts of arrays);
+    returns a report {key: (normwise, failures at GRAD_FLOOR, left out, nonzero)}."""
+    rep = {}
+    for k in keys:
+        a = np.asarray(got[k], np.float64)
+        b = np.asarray(ref[k], np.float64).reshape(a.shape)
+        n, bad, worst = elementwise(a, b, GRAD_RTOL, GRAD_FLOOR)
+        _, bad6, _ = elementwise(a, b, GRAD_RTOL, STRICT_FLOOR)
+        nz = int((b != 0).sum())
+        rep[k] = (normwise(a, b), len(bad), len(bad6), nz)
+        assert normwise(a, b) <= GRAD_RTOL, (k, rep[k])
+        assert len(bad) == 0, (k, rep[k], worst)
+        assert len(bad6) <= max(2, LEFT_OUT_MAX * nz), (k, rep[k])
+    print("gradient check (normwise, fails, left out, nonzero):",
+          {k: (f"{v[0]:.1e}", v[1], v[2], v[3]) for k, v in rep.items()})
+    return rep

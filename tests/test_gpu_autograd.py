@@ -11,7 +11,7 @@ from paper_2405_14342_gb300 import scenes
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from _util import elementwise, normwise  # noqa: E402
+from _util import check_gradients, normwise  # noqa: E402
 
 KEYS = ("xyz", "scale", "quat", "opacity", "rgb", "sem", "exposure")
 
@@ -64,13 +64,7 @@ def per_pixel(planar, cams, C, pix):
 
 def check_against_oracle(m, cams, ex, grads, gout_pix, pix):
     gref = oracle.backward(m, cams, ex, pix, gout_pix)
-    report = {}
-    for k, g in zip(KEYS, grads):
-        a = g.detach().cpu().numpy().astype(np.float64)
-        b = getattr(gref, k).reshape(a.shape)
-        n, bad, worst = elementwise(a, b)
-        report[k] = (normwise(a, b), len(bad), n)
-        assert normwise(a, b) <= 1e-3, (k, report[k])
+    report = check_gradients({k: g.detach().cpu().numpy() for k, g in zip(KEYS, grads)}, gref.as_dict())
     return gref, report
 
 

@@ -5,14 +5,15 @@ outputs, plus the equalities that must hold at any size:
   band of horizon rows, where tile lists are longest) at 1e-4; and the fused
   training step (loss + backward + grid smoothness, the bench's tile and sort
   chunk) with the loss mask on a pixel sample, every gradient tensor against
-  the FP64 oracle (1e-3 normwise);
+  the FP64 oracle (1e-3, normwise and element-wise: _util.check_gradients);
 * batching config (48 views of uneven size in one call): every view equals
   the same view rendered alone, bit for bit, and sampled pixels match the
   oracle;
 * graph-captured step == eager step;
 * differentiation config (4.19M-surfel grid road network, 640x360): GPU
-  gradients of a loss on the 64x64 crop vs the FP64 reverse pass (1e-3
-  normwise) and vs central finite differences of the FP64 forward (eps 1e-4).
+  gradients of a loss on the 64x64 crop vs the FP64 reverse pass (1e-3,
+  normwise and element-wise) and vs central finite differences of the FP64
+  forward (eps 1e-4) on 512 sampled parameters of every type, at 1e-3.
 """
 import numpy as np
 import pytest
@@ -23,7 +24,7 @@ from paper_2405_14342_gb300 import scenes
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from _util import gpu_pixels, gpu_state_T, gpu_tile_lists, normwise, pixel_index, planar_grad_from_pixels  # noqa: E402
+from _util import check_gradients, gpu_pixels, gpu_state_T, gpu_tile_lists, normwise, pixel_index, planar_grad_from_pixels  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -123,11 +124,7 @@ def test_scene_config_training_step_gradients(R, strip):
     ref_g = g.as_dict()
     ref_g["xyz"] = ref_g["xyz"].copy()
     ref_g["xyz"][:, 2] += lam * gs
-    errs = {}
-    for k in ("xyz", "scale", "quat", "opacity", "rgb", "sem", "exposure"):
-        a = grads[k].cpu().numpy().astype(np.float64).reshape(ref_g[k].shape)
-        errs[k] = normwise(a, ref_g[k])
-    assert all(e <= 1e-3 for e in errs.values()), errs
+    check_gradients({k: v.cpu().numpy().reshape(ref_g[k].shape) for k, v in grads.items()}, ref_g)
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
@@ -266,33 +263,63 @@ def test_differentiation_config_crop_gradients(R):
     torch.cuda.synchronize()
     touched = np.nonzero(np.abs(gref.rgb).sum(1))[0]
     assert len(touched) > 50
-    for k in ("xyz", "scale", "quat", "opacity", "rgb", "sem", "exposure"):
-        a = g[k].cpu().numpy().astype(np.float64)
-        b = getattr(gref, k).reshape(a.shape)
-        assert normwise(a, b) < 1e-3, k
-    # central finite differences (eps 1e-4) of the FP64 forward, on a few parameters
-    sub = rng.choice(touched, 8, replace=False)
-    eps = 1e-4
-    rows = []
+    check_gradients({k: v.cpu().numpy() for k, v in g.items()}, gref.as_dict())
+    # Central finite differences (eps = 1e-4) of the FP64 forward on 512
+    # sampled parameters of every type (position, scale, rotation, opacity,
+    # colour, logits; exposure too).  The crop's render depends only on the
+    # surfels whose footprint reaches it, so the oracle's forward runs on that
+    # sub-map (indices keep their order, so depth ties break the same way).
+    pr = oracle.project(m, cams)
+    kap = 2 * np.log(np.maximum(m.opacity.astype(np.float64), 1e-30) / np.float32(1 / 255))
+    rx = np.sqrt(np.maximum(kap * pr.cov[0, :, 0], 0)) + 2.0
+    ry = np.sqrt(np.maximum(kap * pr.cov[0, :, 2], 0)) + 2.0
+    mx, my = pr.mu[0, :, 0], pr.mu[0, :, 1]
+    reach = pr.vis[0] & (mx + rx >= 288) & (mx - rx <= 352) & (my + ry >= 296) & (my - ry <= 360)
+    sub = np.nonzero(reach)[0]
+    ms = scenes.SurfelMap(m.xyz[sub], m.scale[sub], m.quat[sub], m.opacity[sub], m.rgb[sub], m.sem[sub])
+    ok = ref.amb == 0
+    pok = pix[ok]
+    base = oracle.render(ms, cams, ex, pok)
+    assert np.abs(base.out - ref.out[ok]).max() < 1e-12           # the sub-map renders the crop exactly
     tg1 = scenes.Targets(tg.rgb, tg.label, [np.ones((H, W), np.uint8)])
-    pok = pix[ref.amb == 0]
-    base_sig = oracle.render(m, cams, ex, pok).sig
-    for i in sub:
-        for name, kk in (("xyz", 2), ("opacity", 0), ("scale", 0), ("rgb", 1)):
-            vals, flip = [], False
-            for d in (eps, -eps):
-                mp = m.copy()
+    rng = np.random.default_rng(5)
+    pos = {int(i): j for j, i in enumerate(sub)}
+    cand = np.array([i for i in touched if int(i) in pos])
+    kinds = [("xyz", 3), ("scale", 2), ("quat", 4), ("opacity", 1), ("rgb", 3), ("sem", 19)]
+    eps = 1e-4
+    rows, flips = [], 0
+    for smp in range(512):
+        if smp < 2:                                   # the camera's exposure (a, b)
+            name, i, kk = "exposure", 0, smp
+        else:
+            name, width = kinds[smp % len(kinds)]
+            i, kk = int(rng.choice(cand)), int(rng.integers(0, width))
+        vals, flip = [], False
+        for d in (eps, -eps):
+            mp, exp_ = ms.copy(), ex.astype(np.float64).copy()
+            if name == "exposure":
+                exp_[0, kk] += d
+            else:
                 arr = getattr(mp, name).astype(np.float64)
-                arr.reshape(m.n, -1)[i, kk] += d
+                arr.reshape(ms.n, -1)[pos[i], kk] += d
                 setattr(mp, name, arr)
-                Lp, rp = oracle.loss_value(mp, cams, ex, tg1, pok)
-                flip |= not np.array_equal(rp.sig, base_sig)   # a composited list changed: discontinuity
-                vals.append(Lp)
-            if flip:
-                continue
-            fd = (vals[0] - vals[1]) / (2 * eps)
-            gpu = float(g[name].cpu().numpy().reshape(m.n, -1)[i, kk])
-            rows.append((fd, gpu))
-    assert len(rows) >= 10     # samples whose perturbation reorders a list are left out
-    fd = np.array([r[0] for r in rows]); gg = np.array([r[1] for r in rows])
-    assert np.abs(fd - gg).max() <= 2e-3 * np.abs(fd).max() + 1e-9
+            Lp, rp = oracle.loss_value(mp, cams, exp_, tg1, pok)
+            flip |= not np.array_equal(rp.sig, base.sig)   # a composited list changed: discontinuity
+            vals.append(Lp)
+        if flip:
+            flips += 1
+            continue
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        gpu = float(g[name].cpu().numpy().reshape(g[name].shape[0], -1)[i, kk])
+        rows.append((name, fd, gpu))
+    # samples whose perturbation changes a composited list (an alpha crossing
+    # alpha_min at some crop pixel: common for the large near-camera
+    # footprints' geometry) are left out and counted
+    assert flips <= 0.35 * 512 and len(rows) >= 300, (flips, len(rows))
+    fd = np.array([r[1] for r in rows]); gg = np.array([r[2] for r in rows])
+    assert np.abs(fd - gg).max() <= 1e-3 * np.abs(fd).max(), (np.abs(fd - gg).max(), np.abs(fd).max())
+    for name, _ in kinds:                    # and per parameter type, against that type's scale
+        sel = np.array([r[0] == name for r in rows])
+        assert sel.sum() >= 30, (name, sel.sum())
+        assert np.abs(fd[sel] - gg[sel]).max() <= 1e-3 * np.abs(fd[sel]).max(), name
+    print(f"finite differences: {len(rows)} samples compared, {flips} left out (a list changed)")
