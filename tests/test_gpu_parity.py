@@ -195,6 +195,40 @@ def test_tile_lists_are_bit_exact(R):
             np.testing.assert_array_equal(mine, ids[lst[offs[t]:offs[t + 1]]])
 
 
+def test_long_tile_lists_are_exact(R):
+    """Lists of 10,000 entries per tile (several sort chunks): a dense flat
+    patch of equal depths, so the order is decided by the surfel index alone,
+    seen by a small orthographic camera whose every tile holds every surfel;
+    the lists equal the integer binning reference and the forward (which
+    walks the whole list to the transmittance stop) matches the oracle."""
+    n1 = 100
+    g = (np.arange(n1) * 0.012).astype(np.float32)
+    xx, yy = np.meshgrid(g, g)
+    n = n1 * n1
+    rng = np.random.default_rng(8)
+    m = scenes.SurfelMap(xyz=np.stack([xx.ravel(), yy.ravel(), np.zeros(n)], -1).astype(np.float32),
+                         scale=np.full((n, 2), 0.3, np.float32),     # every footprint covers all four tiles
+                         quat=np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                         opacity=np.full(n, 0.05, np.float32), rgb=rng.uniform(0, 1, (n, 3)).astype(np.float32),
+                         sem=rng.normal(0, 1, (n, 2)).astype(np.float32))
+    cam = scenes.bev_camera((0.6, 0.6), 32, res_m=0.05, height_m=10.0)
+    rr = make(R, 2, rec=1 << 15, pairs=1 << 17)
+    st, fr, ext, cnt = gpu_render(R, rr, m, [cam], np.zeros((1, 2)))
+    rec = gpu_records(fr, cnt)
+    rect = gpu_rects(fr, cnt)
+    pr, rg = gpu_tile_lists(fr, cnt)
+    lens = rg[:, 1] - rg[:, 0]
+    assert lens.min() == n, lens
+    ids = np.arange(len(rec))
+    offs, lst = oracle.binning(rect, rec["view"], rec["key"], rec["surfel"].astype(np.int64), [0], [2], 4)
+    assert cnt.n_pairs == offs[-1]
+    for t in range(4):
+        np.testing.assert_array_equal(pr[rg[t, 0]:rg[t, 1]], ids[lst[offs[t]:offs[t + 1]]])
+    # every pixel here composits until the transmittance stop, so more of them
+    # sit in the stop's ambiguity band than in a road scene
+    compare_forward(R, rr, m, [cam], np.zeros((1, 2), np.float32), depth_scale=[10.0], max_band_abs=24)
+
+
 # ------------------------------------------------------------- forward
 
 def test_forward_tiny_matches_oracle(R):

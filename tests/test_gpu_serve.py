@@ -84,18 +84,23 @@ def test_result_alone_equals_result_in_a_mix(env):
     finally:
         srv1.close()
     srv = env["serve"].Server(env["cfg"], env["st"], env["ex"], max_batch_views=16, max_inflight=3,
-                              memory_budget=1 << 30, record_capacity=1 << 18, pair_capacity=1 << 21)
+                              memory_budget=1 << 30, record_capacity=1 << 18, pair_capacity=1 << 22)
     try:
         mix = reqs * 4
         rng = np.random.default_rng(0)
         order = rng.permutation(len(mix))
         tickets = {}
+        # three large requests first keep every stream busy for a few
+        # milliseconds, so the mix arrives while nothing is free and is batched
+        busy = [srv.submit(scenes.bev_camera((3.1, 3.1), 2048, res_m=0.004, height_m=30.0), 7) for _ in range(3)]
         for i in order:
             c, ch = mix[i]
             tickets[i] = srv.submit(c, ch)
         results = {i: srv.wait(t) for i, t in tickets.items()}
+        for t in busy:
+            srv.wait(t)
         st = srv.stats()
-        assert st.completed == len(mix) and st.failed == 0
+        assert st.completed == len(mix) + 3 and st.failed == 0
         assert st.batches < len(mix)                      # requests were batched
     finally:
         srv.close()
