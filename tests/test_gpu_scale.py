@@ -289,12 +289,15 @@ def test_differentiation_config_crop_gradients(R):
     kinds = [("xyz", 3), ("scale", 2), ("quat", 4), ("opacity", 1), ("rgb", 3), ("sem", 19)]
     eps = 1e-4
     rows, flips = [], 0
-    for smp in range(512):
+    gnp = {k: v.cpu().numpy().reshape(v.shape[0], -1) for k, v in g.items()}
+    smp = 0
+    while len(rows) < 512 and smp < 2000:          # 512 compared samples
         if smp < 2:                                   # the camera's exposure (a, b)
             name, i, kk = "exposure", 0, smp
         else:
             name, width = kinds[smp % len(kinds)]
             i, kk = int(rng.choice(cand)), int(rng.integers(0, width))
+        smp += 1
         vals, flip = [], False
         for d in (eps, -eps):
             mp, exp_ = ms.copy(), ex.astype(np.float64).copy()
@@ -313,17 +316,17 @@ def test_differentiation_config_crop_gradients(R):
             flips += 1
             continue
         fd = (vals[0] - vals[1]) / (2 * eps)
-        gpu = float(g[name].cpu().numpy().reshape(g[name].shape[0], -1)[i, kk])
+        gpu = float(gnp[name][i, kk])
         rows.append((name, fd, gpu))
     # samples whose perturbation changes a composited list (an alpha crossing
     # alpha_min at some crop pixel: common for the large near-camera
     # footprints' geometry) or moves a colour across its L1 target are left
-    # out and counted
-    assert flips <= 0.35 * 512 and len(rows) >= 300, (flips, len(rows))
+    # out, counted and replaced by new draws
+    assert len(rows) == 512 and flips <= 0.6 * smp, (len(rows), flips, smp)
     fd = np.array([r[1] for r in rows]); gg = np.array([r[2] for r in rows])
     assert np.abs(fd - gg).max() <= 1e-3 * np.abs(fd).max(), (np.abs(fd - gg).max(), np.abs(fd).max())
     for name, _ in kinds:                    # and per parameter type, against that type's scale
         sel = np.array([r[0] == name for r in rows])
-        assert sel.sum() >= 30, (name, sel.sum())
+        assert sel.sum() >= 40, (name, sel.sum())
         assert np.abs(fd[sel] - gg[sel]).max() <= 1e-3 * np.abs(fd[sel]).max(), name
-    print(f"finite differences: {len(rows)} samples compared, {flips} left out (a list changed)")
+    print(f"finite differences: {len(rows)} samples compared, {flips} draws left out (a list or an L1 sign changed)")
