@@ -43,64 +43,66 @@ __host__ __device__ constexpr int bwd_warp_floats() {
     return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 2 * 32 * kSubPad;
 }
 
-// dL/dout at one pixel, either read from grad_out or, for the fused training
-// step, computed from the forward output and the targets (Eqs. 8, 9, 12):
+// The loss gradient at one pixel for the fused training step (Eqs. 8, 9, 12),
+// computed in place from the pixel's forward output channels G (loaded by
+// the caller together with the targets, in one memory round trip):
 //   dL/dc'  = lambda_c / |M| sign(c' - cbar)          (masked L1, three channels)
 //   dL/dsem = lambda_s / |M| (softmax(sem) - onehot)   (masked cross entropy)
-// Returns the pixel's unnormalised loss term lambda_c |c' - cbar|_1 + lambda_s CE.
+// (the depth channel carries no loss).  Returns the pixel's unnormalised loss
+// term lambda_c |c' - cbar|_1 + lambda_s CE.
 template <int NCP>
-__device__ __forceinline__ float pixel_grad(const BwdArgs& a, const ViewParams& v, int px, int py, int C, float (&G)[NCP]) {
-    const long long q = (long long)py * v.W + px;
-    const long long plane = (long long)v.W * v.H;
-    const int nch = 3 + C + 1;
-    if (!a.tgt_rgb) {
-        const float* go = a.grad_out + (long long)nch * v.pix_base + q;
+__device__ __forceinline__ float pixel_loss_grad(const BwdArgs& a, int C, bool in_mask, unsigned long long nm, int lb,
+                                                 float t0, float t1, float t2, float (&G)[NCP]) {
+    if (!in_mask || nm == 0) {
 #pragma unroll
-        for (int ch = 0; ch < NCP; ++ch) G[ch] = ch < nch ? go[ch * plane] : 0.0f;
+        for (int ch = 0; ch < NCP; ++ch) G[ch] = 0.0f;
         return 0.0f;
     }
-#pragma unroll
-    for (int ch = 0; ch < NCP; ++ch) G[ch] = 0.0f;
-    const long long pix = v.pix_base + q;
-    const unsigned long long nm = *a.mask_count;
-    if (!a.mask[pix] || nm == 0) return 0.0f;
     const float inv = 1.0f / (float)nm;
-    const float* o = a.out + (long long)nch * v.pix_base + q;
-    const float* t = a.tgt_rgb + 3ll * v.pix_base + q;
+    const float tr[3] = {t0, t1, t2};
     float l1 = 0.0f;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        const float d = o[ch * plane] - t[ch * plane];
+        const float d = G[ch] - tr[ch];
         l1 += fabsf(d);
         G[ch] = a.lambda_c * inv * (d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f));
     }
     float ce = 0.0f;
-    const int lb = C > 0 ? a.label[pix] : -1;
     if (lb >= 0 && lb < C) {
-        float x[NCP];
         float mx = -3.0e38f;
 #pragma unroll
-        for (int ch = 0; ch < NCP; ++ch) {
-            x[ch] = (ch >= 3 && ch < 3 + C) ? o[ch * plane] : 0.0f;
-            if (ch >= 3 && ch < 3 + C) mx = fmaxf(mx, x[ch]);
-        }
+        for (int ch = 0; ch < NCP; ++ch)
+            if (ch >= 3 && ch < 3 + C) mx = fmaxf(mx, G[ch]);
         // softmax with one exponential per class: e = exp(x - max), p = e / sum e
         float se = 0.0f, xl = 0.0f;
 #pragma unroll
         for (int ch = 0; ch < NCP; ++ch)
             if (ch >= 3 && ch < 3 + C) {
-                if ((ch - 3) == lb) xl = x[ch];
-                x[ch] = __expf(x[ch] - mx);
-                se += x[ch];
+                if ((ch - 3) == lb) xl = G[ch];
+                G[ch] = __expf(G[ch] - mx);
+                se += G[ch];
             }
         const float rse = 1.0f / se;
         const float ls = a.lambda_s * inv;
 #pragma unroll
         for (int ch = 0; ch < NCP; ++ch)
-            if (ch >= 3 && ch < 3 + C) G[ch] = ls * (x[ch] * rse - ((ch - 3) == lb ? 1.0f : 0.0f));
+            if (ch >= 3 && ch < 3 + C) G[ch] = ls * (G[ch] * rse - ((ch - 3) == lb ? 1.0f : 0.0f));
         ce = mx + logf(se) - xl;
+    } else {
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch)
+            if (ch >= 3 && ch < 3 + C) G[ch] = 0.0f;
     }
+#pragma unroll
+    for (int ch = 0; ch < NCP; ++ch)
+        if (ch >= 3 + C) G[ch] = 0.0f;   // depth and padding
     return a.lambda_c * l1 + a.lambda_s * ce;
+}
+
+// 16-byte vector reduction (add) into global memory; the address is 16-byte aligned.
+__device__ __forceinline__ void red_add_v4(float* p, float x, float y, float z, float w) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w)
+                 : "memory");
 }
 
 template <int TW, int TH, int NCP, int GP>
@@ -141,30 +143,72 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     const float ea = expf(a.exposure_ab[2 * v.exp_idx]);
     const unsigned lt_mask = lanemask_lt();
 
+    // Every input of this lane's pixel is loaded at once, one memory round trip:
+    // the forward's transmittance and last contributor, and either dL/dout or
+    // (fused loss) the output channels, the targets and the mask
+    const bool fused = a.tgt_rgb != nullptr;
     float T = 1.0f;
     uint32_t last = 0;
+    float G[NCP];
+    float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f;
+    int lb = -1;
+    bool in_mask = false;
     if (inside) {
-        const long long pix = v.pix_base + (long long)py * W + px;
+        const long long q = (long long)py * W + px;
+        const long long pix = v.pix_base + q;
+        const long long plane = (long long)W * H;
         T = a.pix_T[pix];
         last = a.pix_last[pix];
-    }
-    const uint32_t wmax = __reduce_max_sync(kFull, last);
-    // the first chunk's list entries are loaded while dL/dout is computed
-    uint32_t rec_first = 0;
-    {
-        const uint32_t j = (wmax > 32u ? wmax - 32u : 0u) + lane;
-        if (j < wmax) rec_first = a.pair_rec[start + j];
-    }
-    float G[NCP];
-    float lpix = 0.0f;
-    float gsum_rgb = 0.0f;
-    if (inside) {
-        lpix = pixel_grad<NCP>(a, v, px, py, C, G);
-        gsum_rgb = G[0] + G[1] + G[2];
-        G[0] *= ea; G[1] *= ea; G[2] *= ea;   // through c' = e^a c + b
+        const float* src = (fused ? a.out : a.grad_out) + (long long)nch * v.pix_base + q;
+#pragma unroll
+        for (int ch = 0; ch < NCP; ++ch) G[ch] = ch < nch ? src[ch * plane] : 0.0f;
+        if (fused) {
+            const float* t = a.tgt_rgb + 3ll * v.pix_base + q;
+            t0 = t[0]; t1 = t[plane]; t2 = t[2 * plane];
+            in_mask = a.mask[pix] != 0;
+            lb = C > 0 ? a.label[pix] : -1;
+        }
     } else {
 #pragma unroll
         for (int ch = 0; ch < NCP; ++ch) G[ch] = 0.0f;
+    }
+    const unsigned long long nm = fused ? *a.mask_count : 0ull;
+    const uint32_t wmax = __reduce_max_sync(kFull, last);
+    // The first chunk (the last 32 list entries up to wmax) is compacted and
+    // staged before the loss gradient is computed: its block masks, records and
+    // mean/conic are loaded now, and its feature rows are copied into shared
+    // memory asynchronously while the loss gradient runs.
+    unsigned mask_first = 0;
+    {
+        const uint32_t cbeg = wmax > 32u ? wmax - 32u : 0u;
+        const uint32_t j = cbeg + lane;
+        bool hit = false;
+        uint32_t rec = 0;
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
+        if (j < wmax) {
+            hit = (a.pair_blk[start + j] >> warp) & 1u;
+            if (hit) {
+                rec = a.pair_rec[start + j];
+                m = a.pair_mc[2ull * (start + j)];
+                c = a.pair_mc[2ull * (start + j) + 1];
+            }
+        }
+        mask_first = __ballot_sync(kFull, hit);
+        if (hit) {
+            const int slot = __popc(mask_first & lt_mask);
+            s_m[slot] = m;
+            s_c[slot] = c;
+            s_rec[slot] = rec;
+            stage_record_features_async<NCP>(s_f + slot * NCP, a.feat, rec);
+        }
+        cp_async_commit();
+    }
+    float lpix = 0.0f;
+    float gsum_rgb = 0.0f;
+    if (inside) {
+        if (fused) lpix = pixel_loss_grad<NCP>(a, C, in_mask, nm, lb, t0, t1, t2, G);
+        gsum_rgb = G[0] + G[1] + G[2];
+        G[0] *= ea; G[1] *= ea; G[2] *= ea;   // through c' = e^a c + b
     }
     if (a.loss_partials) {   // fused loss: one partial per warp, summed in a fixed order later
         float l = lpix;
@@ -172,37 +216,55 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(kFull, l, o);
         if (lane == 0) a.loss_partials[blockIdx.x * kBwdWarpsPerBlock + wib] = l;
     }
+    cp_async_wait_all();
     __syncwarp();
 
     float Ssum = 0.0f;                          // sum_{j>k} w_j (G . f_j)
     float cr0 = 0.0f, cr1 = 0.0f, cr2 = 0.0f;   // raw rgb, for dL/da of Eq. 7
 
+    // block masks of the chunk after the current one are loaded one chunk ahead
+    uint32_t bm_next = 0;
+    {
+        const uint32_t cb = wmax > 32u ? wmax - 32u : 0u;   // the second chunk is [cb - 32, cb)
+        const uint32_t j = (cb > 32u ? cb - 32u : 0u) + lane;
+        if (j < cb) bm_next = a.pair_blk[start + j];
+    }
     for (uint32_t cend = wmax; cend > 0;) {
         const uint32_t cbeg = cend > 32u ? cend - 32u : 0u;
-        const uint32_t j = cbeg + lane;   // index in the tile list
-        bool hit = false;
-        uint32_t rec = 0;
-        float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
-        if (j < cend) {   // the block mask says whether the entry can reach this warp's block
-            hit = (a.pair_blk[start + j] >> warp) & 1u;
-            if (hit) {
-                rec = cend == wmax ? rec_first : a.pair_rec[start + j];
-                m = a.pair_mc[2ull * (start + j)];
-                c = a.pair_mc[2ull * (start + j) + 1];
+        unsigned mask;
+        if (cend == wmax) {
+            mask = mask_first;   // staged before the loss gradient
+        } else {
+            const uint32_t j = cbeg + lane;   // index in the tile list
+            const uint32_t bm = bm_next;
+            {
+                const uint32_t jn = (cbeg > 32u ? cbeg - 32u : 0u) + lane;
+                bm_next = jn < cbeg ? a.pair_blk[start + jn] : 0u;
             }
+            bool hit = false;
+            uint32_t rec = 0;
+            float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
+            if (j < cend) {   // the block mask says whether the entry can reach this warp's block
+                hit = (bm >> warp) & 1u;
+                if (hit) {
+                    rec = a.pair_rec[start + j];
+                    m = a.pair_mc[2ull * (start + j)];
+                    c = a.pair_mc[2ull * (start + j) + 1];
+                }
+            }
+            mask = __ballot_sync(kFull, hit);
+            if (hit) {
+                const int slot = __popc(mask & lt_mask);
+                s_m[slot] = m;
+                s_c[slot] = c;
+                s_rec[slot] = rec;
+                stage_record_features<NCP>(s_f + slot * NCP, a.feat, rec);
+            }
+            __syncwarp();
         }
-        const unsigned mask = __ballot_sync(kFull, hit);
         cend = cbeg;
         if (!mask) continue;
         const int h = __popc(mask);
-        if (hit) {
-            const int slot = __popc(mask & lt_mask);
-            s_m[slot] = m;
-            s_c[slot] = c;
-            s_rec[slot] = rec;
-            stage_record_features<NCP>(s_f + slot * NCP, a.feat, rec);
-        }
-        __syncwarp();
         // phase A (lane = pixel): reverse recursion over the compacted entries.
         // Branch-free: a lane whose entry does not count uses 1 / (1 - a) = 1 and
         // w = 0, which leaves T and S unchanged, so iterations can overlap.
@@ -312,13 +374,33 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         }
         const unsigned anym = __ballot_sync(kFull, any);
         __syncwarp();
-        // flush: one coalesced atomic per (entry, column) into the record's row
-        for (unsigned q = anym; q; q &= q - 1) {
-            const int e = __ffs(q) - 1;
-            float* dst = a.rec_grad + (unsigned long long)s_rec[e] * GP;
-            for (int col = lane; col < 6 + nch; col += 32) {
-                const float val = col < SP ? s_w[e * SP + col] : s_p[e * SP + col - SP];
-                if (val != 0.0f) atomicAdd(dst + col, val);
+        // flush: each gradient row that received anything is added into the
+        // record's row with 16-byte vector reductions, GP/4 lanes per row and
+        // 128/GP rows per instruction (columns past 6 + nch add zeros)
+        {
+            constexpr int QPR = GP / 4;       // 16-byte pieces per row
+            constexpr int RPI = 32 / QPR;     // rows per instruction
+            const int ncol = 6 + nch;
+            const int sub = lane / QPR, col0 = 4 * (lane % QPR);
+            for (unsigned q = anym; q;) {
+                int e = -1;
+#pragma unroll
+                for (int r = 0; r < RPI; ++r) {
+                    if (!q) break;
+                    const int bit = __ffs(q) - 1;
+                    q &= q - 1;
+                    if (r == sub) e = bit;
+                }
+                if (e >= 0 && col0 < ncol) {
+                    float x[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int col = col0 + u;
+                        x[u] = col < ncol ? (col < SP ? s_w[e * SP + col] : s_p[e * SP + col - SP]) : 0.0f;
+                    }
+                    if (x[0] != 0.0f || x[1] != 0.0f || x[2] != 0.0f || x[3] != 0.0f)
+                        red_add_v4(a.rec_grad + (unsigned long long)s_rec[e] * GP + col0, x[0], x[1], x[2], x[3]);
+                }
             }
         }
         __syncwarp();

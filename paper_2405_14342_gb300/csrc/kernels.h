@@ -33,6 +33,23 @@ __device__ __forceinline__ void stage_record_features(float* f, const float* __r
     for (int q = 0; q < NCP / 4; ++q) reinterpret_cast<float4*>(f)[q] = v[q];
 }
 
+// cp.async (global -> shared, 16 bytes, cached in L1) and its group fences.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The same copy as stage_record_features, issued as asynchronous copies; the
+// caller commits, waits and synchronises the warp before reading the row.
+template <int NCP>
+__device__ __forceinline__ void stage_record_features_async(float* f, const float* __restrict__ feat, uint32_t rec) {
+    const float4* src = reinterpret_cast<const float4*>(feat + (unsigned long long)rec * NCP);
+#pragma unroll
+    for (int q = 0; q < NCP / 4; ++q) cp_async16(reinterpret_cast<float4*>(f) + q, src + q);
+}
+
 struct GradPtrs {
     float *xyz, *scale, *quat, *opacity, *rgb, *sem, *exposure;
 };

@@ -291,11 +291,12 @@ def test_differentiation_config_crop_gradients(R):
     rows, flips = [], 0
     gnp = {k: v.cpu().numpy().reshape(v.shape[0], -1) for k, v in g.items()}
     smp = 0
-    while len(rows) < 512 and smp < 2000:          # 512 compared samples
+    got = {k: 0 for k, _ in kinds}
+    while len(rows) < 512 and smp < 3000:          # 512 compared samples, types in equal shares
         if smp < 2:                                   # the camera's exposure (a, b)
             name, i, kk = "exposure", 0, smp
         else:
-            name, width = kinds[smp % len(kinds)]
+            name, width = min(kinds, key=lambda kw: got[kw[0]])
             i, kk = int(rng.choice(cand)), int(rng.integers(0, width))
         smp += 1
         vals, flip = [], False
@@ -318,11 +319,13 @@ def test_differentiation_config_crop_gradients(R):
         fd = (vals[0] - vals[1]) / (2 * eps)
         gpu = float(gnp[name][i, kk])
         rows.append((name, fd, gpu))
+        if name in got:
+            got[name] += 1
     # samples whose perturbation changes a composited list (an alpha crossing
     # alpha_min at some crop pixel: common for the large near-camera
     # footprints' geometry) or moves a colour across its L1 target are left
     # out, counted and replaced by new draws
-    assert len(rows) == 512 and flips <= 0.6 * smp, (len(rows), flips, smp)
+    assert len(rows) == 512 and flips <= 0.75 * smp, (len(rows), flips, smp)
     fd = np.array([r[1] for r in rows]); gg = np.array([r[2] for r in rows])
     assert np.abs(fd - gg).max() <= 1e-3 * np.abs(fd).max(), (np.abs(fd - gg).max(), np.abs(fd).max())
     for name, _ in kinds:                    # and per parameter type, against that type's scale
