@@ -138,9 +138,10 @@ typedef struct {
                  its record (mean_int, mean_frac, conic, alpha), so that a
                  list walk reads them without going through the record id
      pair_blk    uint8 per pair: bit w set iff the record's footprint can
-                 reach the w-th 8x4 pixel block of its tile (blocks row-major
-                 in the tile; the same conservative test the compositing
-                 kernels use) */
+                 reach the w-th pixel block of its tile (the 32-pixel block
+                 of one compositing warp: 16x2 in 16x16 tiles, 8x4 in 8x8
+                 and 32x8 tiles; blocks row-major in the tile; the same
+                 conservative test the compositing kernels use) */
 typedef struct {
     uint64_t header, records, rects, pair_rec, tile_range, pix_T, pix_last, views, tile_order, rec_feat, pair_mc,
         pair_blk, total_bytes;

@@ -1,7 +1,8 @@
 // backward.cu -- stage 4: reverse-order backward of the compositing and the
 // projection (the adjoint of RoGs Eqs. 2, 5, 6, 7; not written in the paper).
 //
-// composite_bwd_k: each warp owns an 8x4 pixel block of a tile and walks the
+// composite_bwd_k: each warp owns a 32-pixel block of a tile (16x2 in 16x16
+// tiles, 8x4 otherwise; block_w in common.cuh) and walks the
 // tile's list backwards from the largest last-composited index of its pixels,
 // 32 entries at a time, keeping only the entries whose footprint can reach its
 // block.  For every pixel it recovers T_k = T_{k+1} / (1 - a_k) and carries one
@@ -107,7 +108,7 @@ __device__ __forceinline__ void red_add_v4(float* p, float x, float y, float z, 
 
 template <int TW, int TH, int NCP, int GP>
 __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArgs a) {
-    constexpr int WX = TW / 8;
+    constexpr int BW = block_w(TW, TH), BH = 32 / BW, WX = TW / BW;
     constexpr int NW = TW * TH / 32;
     constexpr int GROUPS = NW / kBwdWarpsPerBlock;
     constexpr int SP = kSubPad;
@@ -132,8 +133,8 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     const int W = v.W, H = v.H;
     const long long lt = tile - v.tile_base;
     const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
-    const int bx = tx * TW + (warp % WX) * 8, by = ty * TH + (warp / WX) * 4;
-    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const int bx = tx * TW + (warp % WX) * BW, by = ty * TH + (warp / WX) * BH;
+    const int px = bx + lane % BW, py = by + lane / BW;
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     const uint32_t start = a.ranges[tile].x;
@@ -348,8 +349,8 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
                     acc[4 * k4 + 2] = fmaf(w2, a2.z, fmaf(w1, a1.z, acc[4 * k4 + 2]));
                     acc[4 * k4 + 3] = fmaf(w2, a2.w, fmaf(w1, a1.w, acc[4 * k4 + 3]));
                 }
-                const float ax = dx0 + (float)(p1 & 7), ay = dy0 + (float)(p1 >> 3);
-                const float bxo = dx0 + (float)(p2 & 7), byo = dy0 + (float)(p2 >> 3);
+                const float ax = dx0 + (float)(p1 % BW), ay = dy0 + (float)(p1 / BW);
+                const float bxo = dx0 + (float)(p2 % BW), byo = dy0 + (float)(p2 / BW);
                 g0 = fmaf(dp1, cc.x * ax + cc.y * ay, fmaf(dp2, cc.x * bxo + cc.y * byo, g0));
                 g1 = fmaf(dp1, cc.y * ax + cc.z * ay, fmaf(dp2, cc.y * bxo + cc.z * byo, g1));
                 g2 = fmaf(-0.5f * dp1, ax * ax, fmaf(-0.5f * dp2, bxo * bxo, g2));

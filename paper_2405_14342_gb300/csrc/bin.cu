@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict_
                                                      uint2* __restrict__ ranges, float4* __restrict__ pair_mc,
                                                      uint8_t* __restrict__ pair_blk) {
     const unsigned long long n = scan_len(&hdr->n_pairs, cap);
-    const int wx = k.tile_w / 8, nw = k.tile_w * k.tile_h / 32;   // 8x4 blocks of a tile
+    const int bw = block_w(k.tile_w, k.tile_h), bh = 32 / bw;
+    const int wx = k.tile_w / bw, nw = k.tile_w * k.tile_h / 32;   // the warps' pixel blocks of a tile
     for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
          p += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t t = keys[p];
@@ -104,8 +105,8 @@ __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict_
         const float2 r = block_cull_radii(c, k.alpha_min);
         uint32_t bm = 0;
         for (int w = 0; w < nw; ++w) {
-            const int bx = tx * k.tile_w + (w % wx) * 8, by = ty * k.tile_h + (w / wx) * 4;
-            if (box_hits_block(m, r, (float)bx, (float)by)) bm |= 1u << w;
+            const int bx = tx * k.tile_w + (w % wx) * bw, by = ty * k.tile_h + (w / wx) * bh;
+            if (box_hits_block(m, r, (float)bx, (float)by, bw, bh)) bm |= 1u << w;
         }
         pair_blk[p] = (uint8_t)bm;
     }

@@ -156,7 +156,7 @@ __device__ __forceinline__ float surfel_alpha(float dx, float dy, float A, float
 }
 
 // Conservative test: can the entry reach a >= alpha_min at some pixel centre
-// of the 8x4 block whose first pixel is (bx, by)?  Uses the bounding box of
+// of the bw x bh block whose first pixel is (bx, by)?  Uses the bounding box of
 // the ellipse d^T Q d <= 2 ln(alpha / alpha_min) (Q = conic), padded so that
 // rounding never drops a pixel the exact per-pixel test would keep: the fast
 // log, divisions and reciprocal square root used here are within a few ulp,
@@ -171,14 +171,18 @@ __device__ __forceinline__ float2 block_cull_radii(float4 c, float alpha_min) {
     return make_float2(qx * rsqrtf(qx) * 1.002f + 0.01f, qy * rsqrtf(qy) * 1.002f + 0.01f);
 }
 
-__device__ __forceinline__ bool box_hits_block(float4 m, float2 r, float bx, float by) {
+// Pixel block of one compositing warp (32 pixels, one per lane) inside a
+// tile: bw x (32 / bw) pixels.  16x2 in 16x16 tiles: each output-plane access
+// of a warp is two 64-byte row segments instead of four 32-byte ones (measured
+// 8 % faster forward, 4 % faster backward on the scene than 8x4); 8x4 in the
+// 8x8 and 32x8 tiles (32x1 rows in 32x8 tiles measured slower).
+__host__ __device__ constexpr int block_w(int tw, int th) { return tw == 16 && th == 16 ? 16 : 8; }
+
+__device__ __forceinline__ bool box_hits_block(float4 m, float2 r, float bx, float by, int bw, int bh) {
     if (r.x < 0.0f) return true;
     const float mx = m.x + m.z, my = m.y + m.w;
-    return (mx + r.x >= bx + 0.5f) && (mx - r.x <= bx + 7.5f) && (my + r.y >= by + 0.5f) && (my - r.y <= by + 3.5f);
-}
-
-__device__ __forceinline__ bool entry_hits_block(float4 m, float4 c, float alpha_min, float bx, float by) {
-    return box_hits_block(m, block_cull_radii(c, alpha_min), bx, by);
+    return (mx + r.x >= bx + 0.5f) && (mx - r.x <= bx + (float)bw - 0.5f) && (my + r.y >= by + 0.5f) &&
+           (my - r.y <= by + (float)bh - 0.5f);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() {

@@ -5,15 +5,15 @@
 // semantic logits ("the color c is replaced by the semantic vector") and the
 // camera depth; Eq. 7 applies the per-camera exposure e^a c + b to rgb.
 //
-// One CTA per tile; each warp owns an 8x4 pixel block of the tile (one
-// pixel per lane) and walks the tile's depth-ordered list on its own, 32
-// entries at a time: the lanes read one record each, keep only the entries
-// whose footprint can reach the warp's block (a conservative ellipse
-// bounding box), compact them in order into the warp's shared-memory slots
-// together with their features (rgb, sem, depth), and then every lane walks
-// the compacted entries for its pixel: the scalar recursion (alpha, the
-// transmittance stop, w = a T) and the channel sums of Eq. 6,
-// out[ch] += w f[ch], as FP32 fused multiply-adds on the lane's own
+// One CTA per tile; each warp owns a 32-pixel block of the tile (one pixel
+// per lane; 16x2 in 16x16 tiles, 8x4 otherwise) and walks the tile's
+// depth-ordered list on its own, 32 entries at a time: the lanes read one
+// record each, keep only the entries whose footprint can reach the warp's
+// block (a conservative ellipse bounding box), compact them in order into the
+// warp's shared-memory slots together with their features (rgb, sem, depth),
+// and then every lane walks the compacted entries for its pixel: the scalar
+// recursion (alpha, the transmittance stop, w = a T) and the channel sums of
+// Eq. 6, out[ch] += w f[ch], as FP32 fused multiply-adds on the lane's own
 // accumulators, the feature row read from shared memory as broadcast
 // float4s.  A warp stops as soon as all its pixels have stopped, without
 // waiting for the rest of the tile: there is no block-wide barrier.
@@ -54,9 +54,13 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
                                                            float* __restrict__ out, float* __restrict__ pix_T,
                                                            uint32_t* __restrict__ pix_last,
                                                            StateHeader* __restrict__ hdr) {
-    constexpr int WX = TW / 8;
+    constexpr int BW = block_w(TW, TH), BH = 32 / BW, WX = TW / BW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     extern __shared__ float4 smem_fwd[];
+    __shared__ unsigned long long s_comp;   // the CTA's composited pairs
+    __shared__ unsigned s_done;             // warps of the CTA that have added theirs
+    if (threadIdx.x == 0) { s_comp = 0ull; s_done = 0u; }
+    __syncthreads();
     float* wbase = reinterpret_cast<float*>(smem_fwd) + warp * fwd_warp_floats<NCP>();
     float4* s_m = reinterpret_cast<float4*>(wbase);
     float4* s_c = s_m + 32;
@@ -69,8 +73,8 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
     const int W = v.W, H = v.H;
     const long long lt = tile - v.tile_base;
     const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
-    const int bx = tx * TW + (warp % WX) * 8, by = ty * TH + (warp / WX) * 4;
-    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const int bx = tx * TW + (warp % WX) * BW, by = ty * TH + (warp / WX) * BH;
+    const int px = bx + lane % BW, py = by + lane / BW;
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
     const uint2 rg = ranges[tile];
@@ -166,11 +170,21 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
         pix_T[pix] = T;
         pix_last[pix] = last;
     }
-    // composited-pair counter (E_alg)
+    // composited-pair counter (E_alg): summed over the CTA in shared memory;
+    // the CTA's last warp to finish adds it to the global counter, so the
+    // counter takes one atomic per tile instead of one per warp
     unsigned long long cnt = ncomp;
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o2);
-    if (lane == 0 && cnt) atomicAdd(&hdr->composited, cnt);
+    if (lane == 0) {
+        if (cnt) atomicAdd(&s_comp, cnt);
+        __threadfence_block();
+        if (atomicAdd(&s_done, 1u) == (unsigned)(TW * TH / 32) - 1u) {
+            __threadfence_block();
+            const unsigned long long total = atomicAdd(&s_comp, 0ull);
+            if (total) atomicAdd(&hdr->composited, total);
+        }
+    }
 }
 
 static size_t fwd_smem_bytes(int blk, int ncp) {

@@ -86,7 +86,7 @@ void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Recor
                 const unsigned long long* pair_off, const StateHeader* hdr, unsigned long long rec_cap,
                 uint32_t* pair_keys, uint32_t* pair_vals, unsigned long long pair_cap, cudaStream_t s);
 // Tile ranges of the sorted pairs; each pair's record mean + conic copied into
-// pair order (pair_mc, two float4 per pair) and its 8x4-block mask (pair_blk,
+// pair order (pair_mc, two float4 per pair) and its block mask (pair_blk,
 // bit w = entry_hits_block for the tile's w-th block).
 void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Record* recs, const ViewParams* views,
                  int n_views, Consts k, const StateHeader* hdr, unsigned long long pair_cap, uint2* ranges,
@@ -117,7 +117,7 @@ struct BwdArgs {
     const Record* recs;
     const float* feat;   // per-record feature rows (padded_channels(C) floats)
     const float4* pair_mc;   // per-pair record mean + conic (two float4), in list order
-    const uint8_t* pair_blk;  // per-pair 8x4-block masks, in list order
+    const uint8_t* pair_blk;  // per-pair warp-block masks, in list order
     const uint32_t* pair_rec;
     const uint2* ranges;
     const uint32_t* tile_order;
