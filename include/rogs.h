@@ -540,6 +540,17 @@ uint64_t rogs_launch_count(void);
    back cleanly and that nothing leaks.  Process-wide; not for production. */
 void rogs_debug_fail_alloc(int32_t fail_all);
 
+/* Bounds-checked builds (the paper has no counterpart): a library compiled
+   with -DROGS_CHECKED (paper_2405_14342_gb300.build.build(checked=True),
+   librogs_checked.so) tests every index its kernels take from device data
+   -- list entries, record ids, surfel ids, scatter positions -- before use,
+   skips the access if it is out of range and records a failure code (the
+   first one wins; 1xx forward compositing, 2xx backward, 3xx radix sort, 4xx
+   binning).  Returns 1 for such a build and stores (then clears) the code, 0
+   (code 0) for the normal build, whose kernels carry no tests.  Synchronises
+   the device. */
+int32_t rogs_bounds_checked(uint32_t* code);
+
 #ifdef __cplusplus
 }
 #endif

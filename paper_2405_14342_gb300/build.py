@@ -14,6 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build", "librogs")
 LIB = os.path.join(HERE, "librogs.so")
+LIB_CHECKED = os.path.join(HERE, "librogs_checked.so")
 SOURCES = ["api.cu", "project.cu", "sort.cu", "bin.cu", "composite.cu", "backward.cu", "loss.cu", "init.cu",
            "noalloc.cu", "serve.cu", "smooth.cu", "adam.cu", "lidar.cu", "bev.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,10 +38,12 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src, verbose):
-    out = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
+def _compile(src, verbose, checked=False):
+    out = os.path.join(OBJ + ("_checked" if checked else ""), os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", out, "-O3", "-std=c++17", *ARCH, "-lineinfo",
            "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", os.path.join(ROOT, "include")]
+    if checked:
+        cmd += ["-DROGS_CHECKED"]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -49,27 +52,29 @@ def _compile(src, verbose):
     return out, r.stderr
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Build librogs.so, or with checked=True the bounds-checked variant
+    librogs_checked.so (-DROGS_CHECKED, see rogs_bounds_checked in rogs.h)."""
+    lib = LIB_CHECKED if checked else LIB
     deps = _deps()
-    if not force and not _stale(LIB, deps):
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+    if not force and not _stale(lib, deps):
+        return lib
+    os.makedirs(OBJ + ("_checked" if checked else ""), exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, verbose, checked), SOURCES))
     if verbose:
         for _, log in results:
             if log:
                 print(log, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="--verbose" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv, checked="--checked" in sys.argv))

@@ -165,6 +165,8 @@ Consts make_consts(const rogs_config& c) {
     k.tile_w = c.tile_w;
     k.tile_h = c.tile_h;
     k.C = c.num_classes;
+    k.rec_cap = (unsigned long long)c.record_capacity;
+    k.pair_cap = (unsigned long long)c.pair_capacity;
     return k;
 }
 
@@ -451,6 +453,21 @@ rogs_status rogs_reserve(rogs_ctx* ctx, int64_t n_surfels, const rogs_camera* ca
 }
 
 void rogs_debug_fail_alloc(int32_t fail_all) { g_fail_alloc.store(fail_all ? 1 : 0); }
+
+int32_t rogs_bounds_checked(uint32_t* code) {
+#ifdef ROGS_CHECKED
+    cudaDeviceSynchronize();
+    const unsigned w[4] = {check_word_composite(), check_word_backward(), check_word_sort(), check_word_bin()};
+    unsigned c = 0;
+    for (unsigned x : w)
+        if (!c) c = x;
+    if (code) *code = c;
+    return 1;
+#else
+    if (code) *code = 0;
+    return 0;
+#endif
+}
 
 rogs_status rogs_state_layout_of(const rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views,
                                  rogs_state_layout* layout, uint64_t* out_elems) {

@@ -187,11 +187,14 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
         if (j < wmax) {
-            hit = (a.pair_blk[start + j] >> warp) & 1u;
+            hit = (a.pair_blk[start + j] >> warp) & 1u && rogs_ok(start + j < k.pair_cap, 201u);
             if (hit) {
                 rec = a.pair_rec[start + j];
-                m = a.pair_mc[2ull * (start + j)];
-                c = a.pair_mc[2ull * (start + j) + 1];
+                hit = rogs_ok(rec < k.rec_cap, 202u);
+                if (hit) {
+                    m = a.pair_mc[2ull * (start + j)];
+                    c = a.pair_mc[2ull * (start + j) + 1];
+                }
             }
         }
         mask_first = __ballot_sync(kFull, hit);
@@ -246,11 +249,14 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             uint32_t rec = 0;
             float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
             if (j < cend) {   // the block mask says whether the entry can reach this warp's block
-                hit = (bm >> warp) & 1u;
+                hit = (bm >> warp) & 1u && rogs_ok(start + j < k.pair_cap, 203u);
                 if (hit) {
                     rec = a.pair_rec[start + j];
-                    m = a.pair_mc[2ull * (start + j)];
-                    c = a.pair_mc[2ull * (start + j) + 1];
+                    hit = rogs_ok(rec < k.rec_cap, 204u);
+                    if (hit) {
+                        m = a.pair_mc[2ull * (start + j)];
+                        c = a.pair_mc[2ull * (start + j) + 1];
+                    }
                 }
             }
             mask = __ballot_sync(kFull, hit);
@@ -502,6 +508,7 @@ __device__ __forceinline__ void project_bwd_record(const ViewParams* __restrict_
     gr[dcol] = 0.0f;
     const Record rec = recs[r];
     const uint32_t i = rec.surfel;
+    if (!rogs_ok(i < sp.n, 205u)) return;
         if (gp.opacity && g6[5] != 0.0f) atomicAdd(&gp.opacity[i], g6[5]);
 
         const ViewParams& v = views[rec.view];
@@ -633,6 +640,7 @@ __global__ void __launch_bounds__(256) project_bwd_k(const ViewParams* __restric
         uint32_t sid = 0;
         if (r < n) {
             sid = recs[r].surfel;
+            if (!rogs_ok(sid < sp.n, 206u)) sid = 0;
             project_bwd_record(views, sp, recs, rec_grad + r * (unsigned long long)GP, dcol, gp, r);
         }
         const int cnt = n - base < 32ull ? (int)(n - base) : 32;
@@ -667,5 +675,9 @@ void project_bwd(const ViewParams* views, SurfelPtrs sp, const Record* recs, con
     project_bwd_k<<<(int)blocks, 256, 0, s>>>(views, sp, recs, hdr, rec_cap, rec_grad, C, grad_channels(C), g);
     note_launches(1);
 }
+
+#ifdef ROGS_CHECKED
+unsigned check_word_backward() { return rogs_check_word_take(); }
+#endif
 
 }  // namespace rogs

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict
     for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t rec = sorted_rec[j];
+        if (!rogs_ok(rec < rec_cap, 401u)) continue;
         const uint2 r = rects[rec];
         const int x0 = (int)(r.x & 0xffffu), y0 = (int)(r.x >> 16);
         const int x1 = (int)(r.y & 0xffffu), y1 = (int)(r.y >> 16);
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict_
         const uint32_t t = keys[p];
         if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
         if (p + 1 == n || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
+        if (!rogs_ok(pair_rec[p] < k.rec_cap, 402u)) continue;
         const Record& rec = recs[pair_rec[p]];
         const float4* r4 = reinterpret_cast<const float4*>(&rec);
         const float4 m = r4[0], c = r4[1];
@@ -246,5 +248,9 @@ void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool s
     if (sort_ok)
         radix_sort_pairs(ka, va, kb, order, kalt, vb, nullptr, (unsigned long long)n_tiles, 8, hist, s, sort_tile);
 }
+
+#ifdef ROGS_CHECKED
+unsigned check_word_bin() { return rogs_check_word_take(); }
+#endif
 
 }  // namespace rogs

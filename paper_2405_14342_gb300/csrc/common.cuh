@@ -43,7 +43,31 @@ struct ViewsArg {
 struct Consts {
     float t_min, alpha_min, alpha_max, eps, near_plane, box_half_x, box_depth;
     int tile_w, tile_h, C;
+    unsigned long long rec_cap, pair_cap;   // capacities of the state buffer (bounds checks)
 };
+
+// Bounds-checked build.  Compiled with -DROGS_CHECKED, every index the
+// kernels take from device data (list entries, record ids, scatter
+// positions) is tested before use; a failing test records its code in this
+// translation unit's error word (the first code wins) and the access is
+// skipped, so a bad index shows up as a status instead of a fault.  In the
+// normal build rogs_ok() is `true` and the tests compile away.
+#ifdef ROGS_CHECKED
+static __device__ unsigned int g_rogs_check_word;
+__device__ __forceinline__ bool rogs_ok(bool cond, unsigned code) {
+    if (!cond) atomicCAS(&g_rogs_check_word, 0u, code);
+    return cond;
+}
+// Host: read and clear this translation unit's error word.
+static inline unsigned rogs_check_word_take() {
+    unsigned v = 0, z = 0;
+    cudaMemcpyFromSymbol(&v, g_rogs_check_word, sizeof(v));
+    cudaMemcpyToSymbol(g_rogs_check_word, &z, sizeof(z));
+    return v;
+}
+#else
+__device__ __forceinline__ bool rogs_ok(bool, unsigned) { return true; }
+#endif
 
 // 48-byte visible (view, surfel) record; layout documented in rogs.h.
 struct __align__(16) Record {

@@ -101,11 +101,14 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
         if (j < end) {   // the block mask says whether the entry can reach this warp's block
-            hit = (bm >> warp) & 1u;
+            hit = (bm >> warp) & 1u && rogs_ok(j < k.pair_cap, 101u);
             if (hit) {
                 rec = pair_rec[j];
-                m = pair_mc[2ull * j];
-                c = pair_mc[2ull * j + 1];
+                hit = rogs_ok(rec < k.rec_cap, 102u);
+                if (hit) {
+                    m = pair_mc[2ull * j];
+                    c = pair_mc[2ull * j + 1];
+                }
             }
         }
         const unsigned mask = __ballot_sync(kFull, hit);
@@ -255,5 +258,9 @@ void composite_fwd(int tile_w, int tile_h, int C, const ViewParams* views, int n
         launch_fwd_tile<16, 16>(ncp, total_tiles, s, views, n_views, k, sp, recs, feat, pair_mc, pair_blk, pair_rec, ranges, tile_order, exposure_ab, out,
                                 pix_T, pix_last, hdr);
 }
+
+#ifdef ROGS_CHECKED
+unsigned check_word_composite() { return rogs_check_word_take(); }
+#endif
 
 }  // namespace rogs

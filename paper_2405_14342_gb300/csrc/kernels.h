@@ -15,6 +15,13 @@ namespace rogs {
 void note_launches(int n);
 // True while the rogs_debug_fail_alloc test hook makes scratch allocations fail.
 bool debug_alloc_fails();
+#ifdef ROGS_CHECKED
+// Error words of the bounds-checked build, one per translation unit (read and cleared).
+unsigned check_word_composite();
+unsigned check_word_backward();
+unsigned check_word_sort();
+unsigned check_word_bin();
+#endif
 
 struct SurfelPtrs {
     const float *xyz, *scale, *quat, *opacity, *rgb, *sem;

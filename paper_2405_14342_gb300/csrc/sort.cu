@@ -154,8 +154,10 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __r
             if (i < n) {
                 uint32_t d = (key[k] >> shift) & mask;
                 uint32_t pos = wh[warp][d] + rank[k];
-                kout[pos] = key[k];
-                vout[pos] = val[k];
+                if (rogs_ok(pos < n, 301u)) {
+                    kout[pos] = key[k];
+                    vout[pos] = val[k];
+                }
             }
         }
         __syncthreads();
@@ -223,5 +225,9 @@ void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
     else
         radix_passes<16>(kin, vin, kout, vout, kalt, valt, n_ptr, cap, key_bits, hist, row_total, s);
 }
+
+#ifdef ROGS_CHECKED
+unsigned check_word_sort() { return rogs_check_word_take(); }
+#endif
 
 }  // namespace rogs

@@ -156,6 +156,8 @@ def lib():
         L.rogs_serve_get_stats.argtypes = [P, C.POINTER(rogs_serve_stats)]
         L.rogs_serve_set_timeout.argtypes = [P, C.c_double]
         L.rogs_debug_fail_alloc.argtypes = [C.c_int32]
+        L.rogs_bounds_checked.argtypes = [C.POINTER(C.c_uint32)]
+        L.rogs_bounds_checked.restype = C.c_int32
         L.rogs_debug_fail_alloc.restype = None
         L.rogs_serve_close.argtypes = [P]
         L.rogs_serve_close.restype = None
@@ -255,6 +257,14 @@ def rogs_measure_fp32_peak(reps=5, stream=None):
     t, n = C.c_double(), C.c_int32()
     _check(None, lib().rogs_measure_fp32_peak(int(reps), C.byref(t), C.byref(n), _stream(stream)))
     return float(t.value), int(n.value)
+
+
+def rogs_bounds_checked():
+    """(True if the loaded library is the bounds-checked build, first failure code
+    since the last call or 0)."""
+    code = C.c_uint32()
+    chk = lib().rogs_bounds_checked(C.byref(code))
+    return bool(chk), int(code.value)
 
 
 def rogs_debug_fail_alloc(fail_all: bool):

@@ -172,3 +172,70 @@ def test_serve_timeout_is_reported_and_the_server_keeps_serving(env):
     ok = (ref.amb == 0).reshape(cam.height, cam.width)
     out = ref.out.reshape(cam.height, cam.width, -1)
     assert np.abs(r["rgb"].transpose(1, 2, 0)[ok] - out[ok][:, :3]).max() < 1e-4
+
+
+def test_serving_config_requests_at_size():
+    """The serving workload's largest requests on the 4.19M-surfel map: BEV
+    2048^2 (RGB, SEM, ELEV at 0.05 m/px) and 1920x1080 perspective views.
+    Each result is the same alone (plain server) and in a batched mix, bit for
+    bit, and matches the FP64 oracle on sampled pixels."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_14342_gb300 import render, rogs, serve
+    m, field = scenes.grid_road_map(C=19)
+    st = render.SurfelTensors.from_map(m)
+    ex_np = np.zeros((1, 2), np.float32)
+    ex = torch.as_tensor(ex_np, device="cuda")
+    pool = scenes.serve_requests(field, n=400, seed=2)
+    bev = [r for r in pool if r[0].kind == scenes.ORTHO and r[0].width == 2048]
+    big = [next(r for r in bev if r[1] == ch) for ch in (1, 2, 4)]          # RGB, SEM, ELEV
+    big += [r for r in pool if r[0].kind == scenes.PERSP and r[0].width == 1920][:2]
+    assert len(big) == 5
+    others = [r for r in pool if r[0].width <= 640][:12]
+    cfg = rogs.rogs_default_config(19, 1 << 20, 1 << 22)
+    kw = dict(memory_budget=8 << 30, record_capacity=4_000_000, pair_capacity=24_000_000)
+    plain = serve.Server(cfg, st, ex, max_batch_views=1, max_inflight=1, **kw)
+    try:
+        alone = [plain.wait(plain.submit(c, ch), timeout=120.0) for c, ch in big]
+    finally:
+        plain.close()
+    batched = serve.Server(cfg, st, ex, max_batch_views=16, max_inflight=3, **kw)
+    try:
+        mix = big + others
+        order = np.random.default_rng(1).permutation(len(mix))
+        tickets = {int(i): batched.submit(*mix[i]) for i in order}
+        res = {i: batched.wait(t, timeout=120.0) for i, t in tickets.items()}
+        assert batched.stats().failed == 0
+    finally:
+        batched.close()
+    for i in range(len(big)):
+        for k in alone[i]:
+            np.testing.assert_array_equal(res[i][k], alone[i][k])
+    rng = np.random.default_rng(3)
+    for (cam, ch), r in zip(big, alone):
+        H, W = cam.height, cam.width
+        n = 300
+        pix = np.stack([np.zeros(n, np.int32), rng.integers(0, W, n), rng.integers(H // 3 if cam.kind == scenes.PERSP else 0, H, n)],
+                       -1).astype(np.int32)
+        ref = oracle.render(m, [cam], ex_np, pix)
+        ok = ref.amb == 0
+        u, y = pix[:, 1], pix[:, 2]
+        if ch & 1:
+            assert np.abs(r["rgb"][:, y, u].T[ok] - ref.out[ok, :3]).max() < 1e-4
+        if ch & 2:
+            logits = ref.out[:, 3:3 + 19]
+            top2 = np.sort(logits, -1)[:, -2:]
+            clear = ok & (top2[:, 1] - top2[:, 0] > 1e-4)
+            np.testing.assert_array_equal(r["sem"][y, u][clear], logits.argmax(-1)[clear])
+        if ch & 4:
+            cov = 1.0 - ref.T
+            cam_z = -(cam.R.astype(np.float64).T @ cam.t.astype(np.float64))[2]
+            D = ref.out[:, 3 + 19]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                exp = np.where(cov >= 0.5, (cam_z - D / cov) if cam.kind == scenes.ORTHO else D / cov, np.nan)
+            sure = ok & (np.abs(cov - 0.5) > 1e-4)
+            got = r["elev"][y, u]
+            assert np.array_equal(np.isnan(got[sure]), np.isnan(exp[sure]))
+            fin = sure & ~np.isnan(exp)
+            assert np.abs(got[fin] - exp[fin]).max() < 1e-3
+        assert ok.mean() > 0.99
