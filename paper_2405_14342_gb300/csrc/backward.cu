@@ -137,13 +137,25 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     const int px = bx + lane % BW, py = by + lane / BW;
     const bool inside = px < W && py < H;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
-    const uint32_t start = a.ranges[tile].x;
+    const uint2 trange = a.ranges[tile];
+    const uint32_t start = trange.x;
     const int C = k.C;
     const int nch = 3 + C + 1;
     const float amin = k.alpha_min, amax = k.alpha_max;
     const float ea = expf(a.exposure_ab[2 * v.exp_idx]);
     const unsigned lt_mask = lanemask_lt();
 
+    // A tile no surfel reaches (sky, say) passes no gradient to any surfel;
+    // with the fused loss its pixels only count if they are in the mask, so a
+    // warp there reads the mask first and, if none of its pixels is in it,
+    // leaves a zero loss partial without loading anything else.
+    if (a.tgt_rgb && trange.y <= trange.x) {
+        const bool m = inside && a.mask[v.pix_base + (long long)py * W + px] != 0;
+        if (!__any_sync(kFull, m)) {
+            if (a.loss_partials && lane == 0) a.loss_partials[blockIdx.x * kBwdWarpsPerBlock + wib] = 0.0f;
+            return;
+        }
+    }
     // Every input of this lane's pixel is loaded at once, one memory round trip:
     // the forward's transmittance and last contributor, and either dL/dout or
     // (fused loss) the output channels, the targets and the mask
