@@ -238,6 +238,16 @@ def run_ours(args):
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
+    if args.profile_window:
+        # profiling run: only `profile_window` eager training steps between
+        # cudaProfilerStart/Stop (ncu --profile-from-start off), then exit
+        torch.cuda.profiler.start()
+        for k in range(args.profile_window):
+            step(args.warmup + k)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return {"metric": METRIC, "kind": "profile window", "steps": args.profile_window,
+                "config": {"tile": f"{tile[0]}x{tile[1]}", "sort_tile": sort_tile, "timesteps_resident": n_t}}
 
     # ---- batched, graph-captured form (headline): one graph per timestep
     graphs = [rr.train_graph(st, frames[k], exposure, *targets[k], loss, grads, lambda_smooth=LAMBDA_SMOOTH)
@@ -798,6 +808,9 @@ def main():
     ap.add_argument("--timesteps", type=int, default=T_COUNT, help="timesteps kept resident (profiling: fewer)")
     ap.add_argument("--ablation", action="store_true", help="run the initialisation ablation instead of the bench")
     ap.add_argument("--ablation-iters", type=int, default=400)
+    ap.add_argument("--profile-window", type=int, default=0,
+                    help="profiling: run this many eager training steps between cudaProfilerStart/Stop and exit "
+                         "(for ncu --profile-from-start off); no timing")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 800 if args.impl == "ours" and not args.ablation else 32
