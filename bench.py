@@ -414,13 +414,17 @@ def run_ours(args):
     nr = nrec / args.steps
     K = npair / args.steps
     feat = 4 * (3 + C)
+    n_part = frames[0].layout.total_tiles * (tile[0] * tile[1] // 32)
+    # on the side stream beside the forward (not a timed stage): |M| (the mask
+    # count) and the grid smoothness stencil (index map, z rows, dz read-modify-write)
+    side_work = (P * 1 + st.n * (4 + 12 + 8), P * 1.0 + st.n * 12.0)
     stage_work = {
         "composite_fwd": (P * (4 * nch + 8) + 4 * K + nr * (48 + feat), E * (2 * nch + 18)),
         # the loss of Eqs. 8-9 is fused into the backward: it reads out and the targets
         "composite_bwd": (P * (4 * nch + 8 + 17) + 4 * K + nr * (48 + feat + 4 * (6 + nch)),
                           E * (8 * nch + 33) + P * (8 * C + 12)),
-        # |M| (the mask count) and the grid smoothness stencil: index map, z rows, dz read-modify-write
-        "loss": (P * 1 + st.n * (4 + 12 + 8), P * 1.0 + st.n * 12.0),
+        # the fixed-order sum of the backward's per-warp loss partials
+        "loss": (4 * n_part, 1.0 * n_part),
         "project_bwd": (nr * (4 * (6 + nch) + 48 + 40 + 4 * (10 + 3 + C)), nr * 200),
         "cull_project": (st.n * 12 + st.n * 40 + nr * (48 + 8 + 8), st.n * 6 * 12 + nr * 300),
         "depth_sort": (4 * nr * 24, 0.0),
@@ -457,12 +461,13 @@ def run_ours(args):
     # measured step time (graph form)
     t_roof = {k: max(v[0] / (hbm * 1e9), v[1] / (alu_peak * 1e12)) * 1e3 for k, v in stage_work.items()
               if k in stage_ms}
+    t_roof["side_stream"] = max(side_work[0] / (hbm * 1e9), side_work[1] / (alu_peak * 1e12)) * 1e3
     step_roof = {"roofline_ms": round(sum(t_roof.values()), 4), "measured_ms": round(ms / args.steps, 4),
                  "frac": round(sum(t_roof.values()) / (ms / args.steps), 4),
-                 "bytes": round(sum(v[0] for k, v in stage_work.items() if k in stage_ms)),
-                 "flops": round(sum(v[1] for k, v in stage_work.items() if k in stage_ms)),
-                 "binding": {k: ("alu" if stage_work[k][1] / (alu_peak * 1e12) > stage_work[k][0] / (hbm * 1e9)
-                                 else "hbm") for k in t_roof},
+                 "bytes": round(sum(v[0] for k, v in stage_work.items() if k in stage_ms) + side_work[0]),
+                 "flops": round(sum(v[1] for k, v in stage_work.items() if k in stage_ms) + side_work[1]),
+                 "binding": {k: ("alu" if (stage_work.get(k) or side_work)[1] / (alu_peak * 1e12) >
+                                 (stage_work.get(k) or side_work)[0] / (hbm * 1e9) else "hbm") for k in t_roof},
                  "rule": "sum over stages of max(algorithmic bytes / HBM peak, algorithmic FLOPs / FP32 peak)"}
     roof["step"] = step_roof
     roof["alu_peak_tflops_measured"] = round(alu_peak, 2)

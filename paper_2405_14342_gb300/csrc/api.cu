@@ -689,16 +689,29 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     if (lambda_smooth != 0.0f && (!surfels || !surfels->grid_index || surfels->grid_w <= 0 || surfels->grid_h <= 0))
         return fail(ctx, ROGS_ERR_INVALID, "smoothness loss needs the grid index map");
     if (grads->quat && ((uintptr_t)grads->quat & 15u)) return fail(ctx, ROGS_ERR_INVALID, "grad quat alignment");
-    rogs_status st = rogs_render_fwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, stream);
-    if (st != ROGS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     static thread_local ViewsArg va;
     long long total_tiles, total_pix;
     std::string err;
-    make_views(cfg, cams, n_views, va, total_tiles, total_pix, err);   // validated by the forward
+    if (!cams || n_views < 1 || n_views > kMaxViews) return fail(ctx, ROGS_ERR_INVALID, "n_views out of range");
+    if (!make_views(cfg, cams, n_views, va, total_tiles, total_pix, err)) return fail(ctx, ROGS_ERR_INVALID, err);
     const int n_partials = bwd_loss_partials(total_tiles, cfg.tile_w, cfg.tile_h);
-    st = ensure_loss(ctx, total_pix, s, (size_t)n_partials);
+    rogs_status st = ensure_loss(ctx, total_pix, s, (size_t)n_partials);
     if (st == ROGS_OK) st = ensure_rec_grad(ctx, s);
+    if (st != ROGS_OK) return st;
+    // |M| (the mask count of Eqs. 8-9) and lambda_smooth L_smooth (dz into the
+    // gradient, the loss into a scalar the final sum adds) depend only on the
+    // inputs: they run on the side stream while the forward renders, and the
+    // backward waits for them
+    ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+    ROGS_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    mask_count(mask, total_pix, ctx->loss_counter, ctx->side);
+    if (lambda_smooth != 0.0f)
+        smooth_loss(surfels->grid_index, surfels->grid_w, surfels->grid_h, surfels->xyz, lambda_smooth,
+                    ctx->smooth_val, grads->xyz, ctx->smooth_partials, ctx->side);
+    ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+    st = rogs_render_fwd(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, stream);
+    ROGS_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));   // joined even if the forward was refused
     if (st != ROGS_OK) return st;
     const rogs_state_layout L = layout_for(cfg, total_tiles, total_pix);
     const char* sb = (const char*)state;
@@ -709,18 +722,6 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     const SurfelPtrs sp{surfels->xyz, surfels->scale, surfels->quat, surfels->opacity, surfels->rgb, surfels->sem,
                         surfels->n};
     const GradPtrs gp{grads->xyz, grads->scale, grads->quat, grads->opacity, grads->rgb, grads->sem, grads->exposure};
-    prof_mark(ctx, 5, s);
-    mask_count(mask, total_pix, ctx->loss_counter, s);
-    if (lambda_smooth != 0.0f) {
-        // lambda_smooth L_smooth into a scalar the final loss sum adds, dz into the
-        // gradient; independent of the rendering, so it runs on a side stream while
-        // the backward compositing runs (joined before the final loss sum)
-        ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
-        ROGS_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-        smooth_loss(surfels->grid_index, surfels->grid_w, surfels->grid_h, surfels->xyz, lambda_smooth,
-                    ctx->smooth_val, grads->xyz, ctx->smooth_partials, ctx->side);
-        ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
-    }
     BwdArgs a{};
     a.views = views; a.n_views = n_views; a.k = k; a.sp = sp; a.recs = recs;
     a.feat = (const float*)(sb + L.rec_feat);
@@ -738,7 +739,7 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
     prof_mark(ctx, 6, s);
     composite_bwd(cfg.tile_w, cfg.tile_h, total_tiles, a, s);
-    if (lambda_smooth != 0.0f) ROGS_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    prof_mark(ctx, 5, s);
     loss_final(ctx->loss_partials, n_partials, ctx->loss_counter, lambda_smooth != 0.0f ? ctx->smooth_val : nullptr,
                loss, s);
     prof_mark(ctx, 7, s);

@@ -113,9 +113,23 @@ __global__ void __launch_bounds__(1024) loss_final_k(const float* __restrict__ p
                                                      const unsigned long long* __restrict__ counter,
                                                      const float* __restrict__ extra, float* __restrict__ loss) {
     __shared__ float sh[32];
-    float s = 0.0f;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < n; i += 1024) s += partials[i];
+    // thread t sums the float4 groups t, t + 1024, ... (all loads in flight at
+    // once, eight independent accumulators) and the tail; the order is fixed
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const int n4 = n / 4;
+    const float4* p4 = reinterpret_cast<const float4*>(partials);
+    int i = threadIdx.x;
+    for (; i + 1024 < n4; i += 2048) {
+        const float4 x = p4[i], y = p4[i + 1024];
+        a[0] += x.x; a[1] += x.y; a[2] += x.z; a[3] += x.w;
+        a[4] += y.x; a[5] += y.y; a[6] += y.z; a[7] += y.w;
+    }
+    if (i < n4) {
+        const float4 x = p4[i];
+        a[0] += x.x; a[1] += x.y; a[2] += x.z; a[3] += x.w;
+    }
+    if (threadIdx.x < n - 4 * n4) a[0] += partials[4 * n4 + threadIdx.x];
+    float s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
