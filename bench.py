@@ -39,9 +39,9 @@ LAMBDA_SMOOTH = 0.003             # Sec. 4.2 loss weight of the elevation smooth
 # capture, keyed by the sha256 of the source file it was taken from; a
 # different source hash means the kernel changed since and traffic is null.
 NCU_TRAFFIC = {
-    # ncu --set full, one launch of the scene workload (6 x 960x540) per tile shape; see profiles/
-    "composite_bwd": {"sha": "42ccde2bbe9e2e0d", "16x16": 296_062_464 + 54_396_160, "8x8": 325_580_800 + 55_118_080},
-    "composite_fwd": {"sha": "3bbe607479798965", "16x16": 74_588_160 + 255_846_400},
+    # ncu --set full, one launch of the scene workload (6 x 960x540) at 16x16 tiles; see profiles/
+    "composite_bwd": {"sha": "acfe305db1313ffc", "16x16": 294_799_360 + 54_770_944},
+    "composite_fwd": {"sha": "26eb72f4e11095fd", "16x16": 75_555_584 + 255_023_872},
 }
 
 
@@ -415,23 +415,24 @@ def run_ours(args):
     K = npair / args.steps
     feat = 4 * (3 + C)
     n_part = frames[0].layout.total_tiles * (tile[0] * tile[1] // 32)
-    # on the side stream beside the forward (not a timed stage): |M| (the mask
-    # count) and the grid smoothness stencil (index map, z rows, dz read-modify-write)
-    side_work = (P * 1 + st.n * (4 + 12 + 8), P * 1.0 + st.n * 12.0)
+    # on the side stream (not timed stages): |M| (the mask count) and the grid
+    # smoothness stencil (index map, z rows, dz read-modify-write) beside the
+    # forward, the fixed-order sum of the backward's loss partials beside the
+    # projection backward
+    side_work = (P * 1 + st.n * (4 + 12 + 8) + 4 * n_part, P * 1.0 + st.n * 12.0 + n_part)
     stage_work = {
         "composite_fwd": (P * (4 * nch + 8) + 4 * K + nr * (48 + feat), E * (2 * nch + 18)),
         # the loss of Eqs. 8-9 is fused into the backward: it reads out and the targets
         "composite_bwd": (P * (4 * nch + 8 + 17) + 4 * K + nr * (48 + feat + 4 * (6 + nch)),
                           E * (8 * nch + 33) + P * (8 * C + 12)),
-        # the fixed-order sum of the backward's per-warp loss partials
-        "loss": (4 * n_part, 1.0 * n_part),
+
         "project_bwd": (nr * (4 * (6 + nch) + 48 + 40 + 4 * (10 + 3 + C)), nr * 200),
         "cull_project": (st.n * 12 + st.n * 40 + nr * (48 + 8 + 8), st.n * 6 * 12 + nr * 300),
         "depth_sort": (4 * nr * 24, 0.0),
         "pair_emit": (nr * 24 + K * 8, 0.0),
         "tile_sort": (2 * K * 24 + 8 * K, 0.0),
     }
-    stage_ms = {k: (v[0] / max(v[1], 1)) for k, v in prof.items()}   # average per launch
+    stage_ms = {k: (v[0] / v[1]) for k, v in prof.items() if v[1] > 0}   # average per launch (timed stages)
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     b, f = stage_work[dom]
     t = stage_ms[dom] * 1e-3
@@ -501,7 +502,7 @@ def run_ours(args):
                 "ms_per_step": round(ms_plain / args.steps, 4)},
         },
         "roofline": roof,
-        "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof.items()},
+        "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof.items() if v[1] > 0},
         "stages_roofline": stage_roof,
         "counts_per_step": {"records": round(nr), "pairs": round(K), "composited": round(E)},
         "gpu_launches": int(launches),

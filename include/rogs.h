@@ -506,7 +506,8 @@ rogs_status rogs_sort_pairs_noalloc(const uint32_t* keys_in, const uint32_t* val
 
 /* Stages timed by the profiler (CUDA events on the call's stream):
    0 cull + projection (records), 1 depth sort, 2 pair scan + emission,
-   3 tile sort + tile ranges, 4 forward compositing, 5 loss,
+   3 tile sort + tile ranges, 4 forward compositing, 5 loss (the separate
+   rogs_loss; rogs_train_step runs its loss pieces on a side stream, untimed),
    6 backward compositing, 7 projection backward. */
 #define ROGS_N_STAGES 8
 typedef struct {

@@ -53,6 +53,7 @@ struct rogs_ctx {
     float* elev_partials = nullptr;     // one per CTA of the LiDAR elevation loss
     cudaStream_t side = nullptr;        // runs the smoothness loss beside the backward compositing
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;   // the final loss sum beside the projection backward
     LidarScratch lidar{};               // point-cloud hash of rogs_elev_targets
     float* bev_out = nullptr;           // per-batch chunk outputs of rogs_bev_export
     uint8_t* bev_state = nullptr;
@@ -360,7 +361,9 @@ rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
     ROGS_ALLOC(ctx->elev_partials, (size_t)elev_blocks());
     if (st == ROGS_OK && (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
                           cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                          cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess))
+                          cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+                          cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming) != cudaSuccess))
         st = ROGS_ERR_CUDA;
 #undef ROGS_ALLOC
     (void)c0;
@@ -389,6 +392,8 @@ void rogs_destroy(rogs_ctx* ctx) {
         if (p) cudaFree(p);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
+    if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
     if (ctx->side) cudaStreamDestroy(ctx->side);
     for (const ProfEvent& pe : ctx->prof_pending) {
         cudaEventDestroy(pe.a);
@@ -739,12 +744,17 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
     prof_mark(ctx, 6, s);
     composite_bwd(cfg.tile_w, cfg.tile_h, total_tiles, a, s);
-    prof_mark(ctx, 5, s);
+    // the final loss sum (its partials are complete) runs on the side stream
+    // beside the projection backward; the call's stream waits for both
+    ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_fork2, s));
+    ROGS_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork2, 0));
     loss_final(ctx->loss_partials, n_partials, ctx->loss_counter, lambda_smooth != 0.0f ? ctx->smooth_val : nullptr,
-               loss, s);
+               loss, ctx->side);
+    ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_join2, ctx->side));
     prof_mark(ctx, 7, s);
     project_bwd(views, sp, recs, hdr, (unsigned long long)cfg.record_capacity, ctx->rec_grad, cfg.num_classes, gp, s);
     prof_mark(ctx, -1, s);
+    ROGS_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join2, 0));
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
 }
