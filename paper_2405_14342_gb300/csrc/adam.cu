@@ -39,6 +39,7 @@ __device__ __forceinline__ void adam_one(const AdamArgs& a, float& p, float& g, 
 // One thread per 4-element chunk of a group (grid-stride over all chunks):
 // float4 loads and stores where the group allows them, else four scalars.
 __global__ void __launch_bounds__(256) adam_k(AdamArgs a) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     const long long total = a.pre[a.n_groups];
     int gi = 0;
     for (long long k = blockIdx.x * 256ll + threadIdx.x; k < total; k += (long long)gridDim.x * 256) {
@@ -101,7 +102,7 @@ void adam_step(const rogs_adam_group* groups, int n_groups, int step, float b1, 
     if (total == 0) return;
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    adam_k<<<(int)blocks, 256, 0, s>>>(a);
+    launch_pdl(adam_k, dim3((int)blocks), dim3(256), 0, s, a);
     note_launches(1);
 }
 

@@ -108,6 +108,7 @@ __device__ __forceinline__ void red_add_v4(float* p, float x, float y, float z, 
 
 template <int TW, int TH, int NCP, int GP>
 __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArgs a) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     constexpr int BW = block_w(TW, TH), BH = 32 / BW, WX = TW / BW;
     constexpr int NW = TW * TH / 32;
     constexpr int GROUPS = NW / kBwdWarpsPerBlock;
@@ -482,7 +483,7 @@ static void launch_bwd_tile(int ncp, long long total_tiles, const BwdArgs& a, cu
 #define ROGS_BWD(NCP, GP)                                                                           \
     do {                                                                                            \
         bwd_attr<TW, TH, NCP, GP>();                                                                \
-        composite_bwd_k<TW, TH, NCP, GP><<<grid, 32 * kBwdWarpsPerBlock, bwd_smem_bytes(NCP), s>>>(a); \
+        launch_pdl(composite_bwd_k<TW, TH, NCP, GP>, dim3(grid), dim3(32 * kBwdWarpsPerBlock), bwd_smem_bytes(NCP), s, a); \
         note_launches(1);                                                                           \
     } while (0)
     switch (ncp) {
@@ -640,6 +641,7 @@ __global__ void __launch_bounds__(256) project_bwd_k(const ViewParams* __restric
                                                      const Record* __restrict__ recs,
                                                      const StateHeader* __restrict__ hdr, unsigned long long rec_cap,
                                                      float* __restrict__ rec_grad, int C, int GP, GradPtrs gp) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     unsigned long long n = hdr->n_records;
     if (n > rec_cap) n = rec_cap;
     const int lane = threadIdx.x & 31;
@@ -684,7 +686,7 @@ void project_bwd(const ViewParams* views, SurfelPtrs sp, const Record* recs, con
     unsigned long long blocks = (rec_cap + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    project_bwd_k<<<(int)blocks, 256, 0, s>>>(views, sp, recs, hdr, rec_cap, rec_grad, C, grad_channels(C), g);
+    launch_pdl(project_bwd_k, dim3((int)blocks), dim3(256), 0, s, views, sp, recs, hdr, rec_cap, rec_grad, C, grad_channels(C), g);
     note_launches(1);
 }
 

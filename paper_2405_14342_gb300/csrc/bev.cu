@@ -13,6 +13,7 @@ namespace rogs {
 
 __global__ void __launch_bounds__(256) stitch_k(StitchViews sv, int n_views, int nch, const float* __restrict__ out,
                                                 float* __restrict__ image, int W, int H) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     const long long total = sv.pix_end[n_views - 1] * (long long)nch;
     for (long long k = blockIdx.x * 256ll + threadIdx.x; k < total; k += (long long)gridDim.x * 256) {
         // view of element k: views are laid out [view][plane][pixel]
@@ -34,7 +35,7 @@ void stitch_views(const StitchViews& sv, int n_views, int nch, const float* out,
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    stitch_k<<<(int)blocks, 256, 0, s>>>(sv, n_views, nch, out, image, W, H);
+    launch_pdl(stitch_k, dim3((int)blocks), dim3(256), 0, s, sv, n_views, nch, out, image, W, H);
     note_launches(1);
 }
 

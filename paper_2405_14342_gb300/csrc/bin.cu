@@ -26,6 +26,7 @@ struct RectTilesF {
 };
 
 __global__ void finalize_pairs_k(StateHeader* hdr, unsigned long long cap) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     unsigned long long need = hdr->need_pairs;
     hdr->n_pairs = need < cap ? need : cap;
     if (need > cap) hdr->status |= kStatusPairOverflow;
@@ -36,7 +37,7 @@ void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeade
                 StateHeader* hdr, unsigned long long pair_cap, cudaStream_t s) {
     device_exclusive_scan<RectTilesF, unsigned long long>(RectTilesF{sorted_rec, rects}, &hdr_n_records->n_records,
                                                           rec_cap, tile_sums, pair_off, &hdr->need_pairs, s);
-    finalize_pairs_k<<<1, 1, 0, s>>>(hdr, pair_cap);
+    launch_pdl(finalize_pairs_k, dim3(1), dim3(1), 0, s, hdr, pair_cap);
     note_launches(1);
 }
 
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict
                                                     const StateHeader* __restrict__ hdr, unsigned long long rec_cap,
                                                     uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals,
                                                     unsigned long long pair_cap) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     const unsigned long long n = scan_len(&hdr->n_records, rec_cap);
     for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
@@ -75,7 +77,7 @@ void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Recor
     unsigned long long blocks = (rec_cap + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    emit_pairs_k<<<(int)blocks, 256, 0, s>>>(views, sorted_rec, recs, rects, pair_off, hdr, rec_cap, pair_keys,
+    launch_pdl(emit_pairs_k, dim3((int)blocks), dim3(256), 0, s, views, sorted_rec, recs, rects, pair_off, hdr, rec_cap, pair_keys,
                                               pair_vals, pair_cap);
     note_launches(1);
 }
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict_
                                                      const StateHeader* __restrict__ hdr, unsigned long long cap,
                                                      uint2* __restrict__ ranges, float4* __restrict__ pair_mc,
                                                      uint8_t* __restrict__ pair_blk) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     const unsigned long long n = scan_len(&hdr->n_pairs, cap);
     const int bw = block_w(k.tile_w, k.tile_h), bh = 32 / bw;
     const int wx = k.tile_w / bw, nw = k.tile_w * k.tile_h / 32;   // the warps' pixel blocks of a tile
@@ -120,7 +123,7 @@ void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Re
     unsigned long long blocks = (pair_cap + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    tile_ranges_k<<<(int)blocks, 256, 0, s>>>(sorted_tile, pair_rec, recs, views, n_views, k, hdr, pair_cap, ranges,
+    launch_pdl(tile_ranges_k, dim3((int)blocks), dim3(256), 0, s, sorted_tile, pair_rec, recs, views, n_views, k, hdr, pair_cap, ranges,
                                               pair_mc, pair_blk);
     note_launches(1);
 }
@@ -138,6 +141,7 @@ __device__ __forceinline__ uint32_t tile_class_key(const uint2* __restrict__ ran
 __global__ void __launch_bounds__(256) tile_keys_k(const uint2* __restrict__ ranges, long long n_tiles,
                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                    uint32_t* __restrict__ order, int sort_ok) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_tiles;
          t += (long long)gridDim.x * blockDim.x) {
         if (!sort_ok) {
@@ -161,6 +165,7 @@ constexpr long long kOrderOneBlockMax = 32768;
 __global__ void __launch_bounds__(kOrderThreads) tile_order_block_k(const uint2* __restrict__ ranges,
                                                                     long long n_tiles,
                                                                     uint32_t* __restrict__ order) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ uint32_t wh[kOrderThreads / 32][256];   // per-warp counts, then write positions
     __shared__ uint32_t scan_w[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -235,7 +240,7 @@ void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool s
                  uint32_t* kb, uint32_t* vb, uint32_t* kalt, uint32_t* hist, cudaStream_t s, int sort_tile) {
     if (sort_ok && n_tiles <= kOrderOneBlockMax) {
         if (n_tiles > 0) {
-            tile_order_block_k<<<1, kOrderThreads, 0, s>>>(ranges, n_tiles, order);
+            launch_pdl(tile_order_block_k, dim3(1), dim3(kOrderThreads), 0, s, ranges, n_tiles, order);
             note_launches(1);
         }
         return;
@@ -243,7 +248,7 @@ void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool s
     long long blocks = (n_tiles + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks < 1) blocks = 1;
-    tile_keys_k<<<(int)blocks, 256, 0, s>>>(ranges, n_tiles, ka, va, order, sort_ok ? 1 : 0);
+    launch_pdl(tile_keys_k, dim3((int)blocks), dim3(256), 0, s, ranges, n_tiles, ka, va, order, sort_ok ? 1 : 0);
     note_launches(1);
     if (sort_ok)
         radix_sort_pairs(ka, va, kb, order, kalt, vb, nullptr, (unsigned long long)n_tiles, 8, hist, s, sort_tile);

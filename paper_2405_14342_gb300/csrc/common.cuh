@@ -22,6 +22,29 @@
 
 namespace rogs {
 
+// Programmatic dependent launch.  The library's kernels are launched with
+// programmatic stream serialization: a kernel's blocks may be scheduled while
+// the previous kernel of the stream drains its last blocks, and every kernel
+// waits at its top (griddepcontrol.wait) until that previous kernel has
+// completed and its memory is visible, so the overlap hides launch latency
+// and changes no result.  Outside such a launch the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline void launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+
 constexpr int kMaxViews = ROGS_MAX_VIEWS;
 constexpr unsigned kFull = 0xffffffffu;
 

@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
                                                            float* __restrict__ out, float* __restrict__ pix_T,
                                                            uint32_t* __restrict__ pix_last,
                                                            StateHeader* __restrict__ hdr) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     constexpr int BW = block_w(TW, TH), BH = 32 / BW, WX = TW / BW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     extern __shared__ float4 smem_fwd[];
@@ -228,7 +229,7 @@ static void launch_fwd_tile(int ncp, long long total_tiles, cudaStream_t s, cons
 #define ROGS_FWD(NCP)                                                                                          \
     do {                                                                                                       \
         fwd_attr<TW, TH, NCP>();                                                                               \
-        composite_fwd_k<TW, TH, NCP><<<grid, TW * TH, fwd_smem_bytes(TW * TH, NCP), s>>>(                     \
+        launch_pdl(composite_fwd_k<TW, TH, NCP>, dim3(grid), dim3(TW * TH), fwd_smem_bytes(TW * TH, NCP), s,                      \
             views, n_views, k, sp, recs, feat, pair_mc, pair_blk, pair_rec, ranges, tile_order, exposure_ab, out, \
             pix_T, pix_last, hdr);                                                                             \
         note_launches(1);                                                                                      \

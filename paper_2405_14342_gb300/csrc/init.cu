@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(kInitThreads) init_k(const float* __restrict__
                                                        int exact_plane, float* __restrict__ out_z,
                                                        float* __restrict__ out_quat,
                                                        int32_t* __restrict__ out_nearest) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ float2 sp[kPoseChunk];
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float x = 0.0f, y = 0.0f;
@@ -87,7 +88,7 @@ void init_from_poses(const float* grid_xy, long long n, const float* poses_dev, 
                      float* out_z, float* out_quat, int32_t* out_nearest, cudaStream_t s) {
     if (n <= 0) return;
     const long long blocks = (n + kInitThreads - 1) / kInitThreads;
-    init_k<<<(unsigned)blocks, kInitThreads, 0, s>>>(grid_xy, n, poses_dev, n_poses, exact_plane, out_z, out_quat,
+    launch_pdl(init_k, dim3((unsigned)blocks), dim3(kInitThreads), 0, s, grid_xy, n, poses_dev, n_poses, exact_plane, out_z, out_quat,
                                                      out_nearest);
     note_launches(1);
 }

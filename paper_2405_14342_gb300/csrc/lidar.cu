@@ -21,6 +21,7 @@ __device__ __forceinline__ uint32_t cell_bucket(int cx, int cy, uint32_t mask) {
 __global__ void __launch_bounds__(256) lidar_hash_k(const float* __restrict__ pts, long long m, float inv_cell,
                                                     uint32_t mask, uint32_t* __restrict__ keys,
                                                     uint32_t* __restrict__ vals) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     for (long long i = blockIdx.x * 256ll + threadIdx.x; i < m; i += (long long)gridDim.x * 256) {
         const int cx = (int)floorf(pts[3 * i] * inv_cell), cy = (int)floorf(pts[3 * i + 1] * inv_cell);
         keys[i] = cell_bucket(cx, cy, mask);
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(256) lidar_ranges_k(const uint32_t* __restrict
                                                       const uint32_t* __restrict__ order,
                                                       const float* __restrict__ pts, long long m,
                                                       uint2* __restrict__ ranges, float4* __restrict__ sorted) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     for (long long p = blockIdx.x * 256ll + threadIdx.x; p < m; p += (long long)gridDim.x * 256) {
         const uint32_t b = keys[p];
         if (p == 0 || keys[p - 1] != b) ranges[b].x = (uint32_t)p;
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(256) lidar_nearest_k(const float* __restrict__
                                                        const float4* __restrict__ sorted,
                                                        const uint2* __restrict__ ranges, uint32_t mask,
                                                        float inv_cell, float r2, float* __restrict__ zbar) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
         const float x = xyz[3 * i], y = xyz[3 * i + 1];
         const int cx = (int)floorf(x * inv_cell), cy = (int)floorf(y * inv_cell);
@@ -74,6 +77,7 @@ __global__ void __launch_bounds__(256) lidar_nearest_k(const float* __restrict__
 __global__ void __launch_bounds__(256) elev_k(const float* __restrict__ xyz, long long n,
                                               const float* __restrict__ zbar, float lambda,
                                               float* __restrict__ grad_xyz, float* __restrict__ partials) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ float sh[8];
     float acc = 0.0f;
     for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
@@ -95,6 +99,7 @@ __global__ void __launch_bounds__(256) elev_k(const float* __restrict__ xyz, lon
 }
 
 __global__ void elev_final_k(const float* __restrict__ partials, int n, float lambda, float* __restrict__ loss) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     float s = 0.0f;
     for (int i = threadIdx.x; i < n; i += 32) s += partials[i];
 #pragma unroll
@@ -124,14 +129,14 @@ void lidar_targets(const float* xyz, long long n, const float* pts, long long m,
     const float inv_cell = 1.0f / cell;
     cudaMemsetAsync(w.ranges, 0, sizeof(uint2) << bits, s);
     if (m > 0) {
-        lidar_hash_k<<<grid_for(m), 256, 0, s>>>(pts, m, inv_cell, mask, w.keys, w.vals);
+        launch_pdl(lidar_hash_k, dim3(grid_for(m)), dim3(256), 0, s, pts, m, inv_cell, mask, w.keys, w.vals);
         radix_sort_pairs(w.keys, w.vals, w.skeys, w.svals, w.kalt, w.valt, nullptr, (unsigned long long)m, bits,
                          w.hist, s, 2048);
-        lidar_ranges_k<<<grid_for(m), 256, 0, s>>>(w.skeys, w.svals, pts, m, w.ranges, w.sorted);
+        launch_pdl(lidar_ranges_k, dim3(grid_for(m)), dim3(256), 0, s, w.skeys, w.svals, pts, m, w.ranges, w.sorted);
         note_launches(2);
     }
     if (n > 0) {
-        lidar_nearest_k<<<grid_for(n), 256, 0, s>>>(xyz, n, w.sorted, w.ranges, mask, inv_cell, radius * radius,
+        launch_pdl(lidar_nearest_k, dim3(grid_for(n)), dim3(256), 0, s, xyz, n, w.sorted, w.ranges, mask, inv_cell, radius * radius,
                                                      zbar);
         note_launches(1);
     }
@@ -142,8 +147,8 @@ void elev_loss(const float* xyz, long long n, const float* zbar, float lambda, f
     long long nb = (n + 255) / 256;
     if (nb > elev_blocks()) nb = elev_blocks();
     if (nb < 1) nb = 1;
-    elev_k<<<(int)nb, 256, 0, s>>>(xyz, n, zbar, lambda, grad_xyz, partials);
-    elev_final_k<<<1, 32, 0, s>>>(partials, (int)nb, lambda, loss);
+    launch_pdl(elev_k, dim3((int)nb), dim3(256), 0, s, xyz, n, zbar, lambda, grad_xyz, partials);
+    launch_pdl(elev_final_k, dim3(1), dim3(32), 0, s, partials, (int)nb, lambda, loss);
     note_launches(2);
 }
 

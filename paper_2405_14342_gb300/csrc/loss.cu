@@ -27,6 +27,7 @@ __device__ __forceinline__ int view_of_pixel(const ViewParams* views, int n_view
 
 __global__ void __launch_bounds__(kLossThreads) mask_count_k(const uint8_t* __restrict__ mask, long long n,
                                                              unsigned long long* __restrict__ counter) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ unsigned int sh[kLossThreads / 32];
     unsigned int c = 0;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restr
                                                        const uint8_t* __restrict__ mask, float lambda_c,
                                                        float lambda_s, const unsigned long long* __restrict__ counter,
                                                        float* __restrict__ grad_out, float* __restrict__ partials) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ float sh[kLossThreads / 32];
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     float l = 0.0f;
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restr
 __global__ void __launch_bounds__(1024) loss_final_k(const float* __restrict__ partials, int n,
                                                      const unsigned long long* __restrict__ counter,
                                                      const float* __restrict__ extra, float* __restrict__ loss) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ float sh[32];
     // thread t sums the float4 groups t, t + 1024, ... (all loads in flight at
     // once, eight independent accumulators) and the tail; the order is fixed
@@ -153,10 +156,10 @@ void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, 
     cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     int gc = nb < 152 * 8 ? nb : 152 * 8;
     if (gc < 1) gc = 1;
-    mask_count_k<<<gc, kLossThreads, 0, s>>>(mask, total_pixels, counter);
-    loss_k<<<nb > 0 ? nb : 1, kLossThreads, 0, s>>>(views, n_views, total_pixels, C, out, tgt_rgb, label, mask,
+    launch_pdl(mask_count_k, dim3(gc), dim3(kLossThreads), 0, s, mask, total_pixels, counter);
+    launch_pdl(loss_k, dim3(nb > 0 ? nb : 1), dim3(kLossThreads), 0, s, views, n_views, total_pixels, C, out, tgt_rgb, label, mask,
                                                     lambda_c, lambda_s, counter, grad_out, partials);
-    loss_final_k<<<1, 1024, 0, s>>>(partials, nb, counter, nullptr, loss);
+    launch_pdl(loss_final_k, dim3(1), dim3(1024), 0, s, partials, nb, counter, nullptr, loss);
     note_launches(3);
     (void)n_blocks_cap;
 }
@@ -166,13 +169,13 @@ void mask_count(const uint8_t* mask, long long total_pixels, unsigned long long*
     long long nb = (total_pixels + kLossThreads - 1) / kLossThreads;
     int gc = (int)(nb < 152 * 8 ? nb : 152 * 8);
     if (gc < 1) gc = 1;
-    mask_count_k<<<gc, kLossThreads, 0, s>>>(mask, total_pixels, counter);
+    launch_pdl(mask_count_k, dim3(gc), dim3(kLossThreads), 0, s, mask, total_pixels, counter);
     note_launches(1);
 }
 
 void loss_final(const float* partials, int n, const unsigned long long* counter, const float* extra, float* loss,
                 cudaStream_t s) {
-    loss_final_k<<<1, 1024, 0, s>>>(partials, n, counter, extra, loss);
+    launch_pdl(loss_final_k, dim3(1), dim3(1024), 0, s, partials, n, counter, extra, loss);
     note_launches(1);
 }
 

@@ -131,6 +131,7 @@ constexpr int kProjThreads = 256;
 
 __global__ void __launch_bounds__(kProjThreads) cull_k(const ViewParams* __restrict__ views, int n_views, Consts k,
                                                         SurfelPtrs sp, uint32_t* __restrict__ bits, long long n_words) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     extern __shared__ ViewParams sv[];
     load_views_smem(sv, views, n_views);
     const int lane = threadIdx.x & 31;
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(kProjThreads) project_k(const ViewParams* __re
                                                            float* __restrict__ feat, int ncp,
                                                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                            unsigned long long rec_cap) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     extern __shared__ ViewParams sv[];
     load_views_smem(sv, views, n_views);
     const int lane = threadIdx.x & 31;
@@ -227,6 +229,7 @@ __global__ void __launch_bounds__(kProjThreads) project_k(const ViewParams* __re
 }
 
 __global__ void upload_views_k(ViewsArg va, int n_views, ViewParams* dst, StateHeader* hdr) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     const int words = n_views * (int)(sizeof(ViewParams) / 4);
     const uint32_t* src = reinterpret_cast<const uint32_t*>(va.v);
     uint32_t* d = reinterpret_cast<uint32_t*>(dst);
@@ -239,7 +242,7 @@ __global__ void upload_views_k(ViewsArg va, int n_views, ViewParams* dst, StateH
 }
 
 void upload_views(const ViewsArg& va, int n_views, ViewParams* dst, StateHeader* hdr, cudaStream_t s) {
-    upload_views_k<<<1, 256, 0, s>>>(va, n_views, dst, hdr);
+    launch_pdl(upload_views_k, dim3(1), dim3(256), 0, s, va, n_views, dst, hdr);
     note_launches(1);
 }
 
@@ -253,7 +256,7 @@ static int grid_for_words(long long n_words) {
 void cull_views(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, uint32_t* bits, long long n_words,
                 cudaStream_t s) {
     size_t sm = sizeof(ViewParams) * (size_t)n_views;
-    cull_k<<<grid_for_words(n_words), kProjThreads, sm, s>>>(views, n_views, k, sp, bits, n_words);
+    launch_pdl(cull_k, dim3(grid_for_words(n_words)), dim3(kProjThreads), sm, s, views, n_views, k, sp, bits, n_words);
     note_launches(1);
 }
 
@@ -265,6 +268,7 @@ struct PopcF {
 size_t scan_tile_sums_words(unsigned long long cap) { return (size_t)scan_tiles_for(cap) * 2 + 2; }
 
 __global__ void finalize_records_k(StateHeader* hdr, unsigned long long cap) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     unsigned long long need = hdr->need_records;
     hdr->n_records = need < cap ? need : cap;
     if (need > cap) hdr->status |= kStatusRecordOverflow;
@@ -274,12 +278,12 @@ void scan_visible(const uint32_t* bits, long long n_words_total, uint32_t* word_
                   StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s) {
     device_exclusive_scan<PopcF, uint32_t>(PopcF{bits}, nullptr, (unsigned long long)n_words_total, tile_sums,
                                            word_off, &hdr->need_records, s);
-    finalize_records_k<<<1, 1, 0, s>>>(hdr, rec_cap);
+    launch_pdl(finalize_records_k, dim3(1), dim3(1), 0, s, hdr, rec_cap);
     note_launches(1);
 }
 
 void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s) {
-    finalize_records_k<<<1, 1, 0, s>>>(hdr, rec_cap);
+    launch_pdl(finalize_records_k, dim3(1), dim3(1), 0, s, hdr, rec_cap);
     note_launches(1);
 }
 
@@ -287,7 +291,7 @@ void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs 
                      const uint32_t* word_off, long long n_words, Record* recs, uint2* rects, float* feat,
                      uint32_t* keys, uint32_t* vals, unsigned long long rec_cap, cudaStream_t s) {
     size_t sm = sizeof(ViewParams) * (size_t)n_views;
-    project_k<<<grid_for_words(n_words), kProjThreads, sm, s>>>(views, n_views, k, sp, bits, word_off, n_words, recs,
+    launch_pdl(project_k, dim3(grid_for_words(n_words)), dim3(kProjThreads), sm, s, views, n_views, k, sp, bits, word_off, n_words, recs,
                                                                 rects, feat, padded_channels(k.C), keys, vals,
                                                                 rec_cap);
     note_launches(1);

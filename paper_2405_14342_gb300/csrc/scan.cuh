@@ -60,6 +60,7 @@ __device__ __forceinline__ unsigned long long scan_len(const unsigned long long*
 template <class F, class T>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_k(F f, const unsigned long long* n_ptr,
                                                                unsigned long long cap, T* tile_sums) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ T sh[33];
     const unsigned long long n = scan_len(n_ptr, cap);
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_k(F f, const unsigne
 // One block: exclusive scan of n_tiles tile sums in place; *total = sum.
 template <class T>
 __global__ void __launch_bounds__(kScanThreads) scan_tiles_k(T* tile_sums, int n_tiles, unsigned long long* total) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ T sh[33];
     T carry = 0;
     for (int base = 0; base < n_tiles; base += kScanThreads) {
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_k(T* tile_sums, int n
 template <class F, class T>
 __global__ void __launch_bounds__(kScanThreads) scan_down_k(F f, const unsigned long long* n_ptr,
                                                              unsigned long long cap, const T* tile_offs, T* out) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ T sh[33];
     const unsigned long long n = scan_len(n_ptr, cap);
     const unsigned long long base = (unsigned long long)blockIdx.x * kScanTile;
@@ -127,9 +130,9 @@ template <class F, class T>
 inline void device_exclusive_scan(F f, const unsigned long long* n_ptr, unsigned long long cap, T* tile_sums,
                                   T* out, unsigned long long* total, cudaStream_t s) {
     int nt = scan_tiles_for(cap);
-    scan_reduce_k<F, T><<<nt, kScanThreads, 0, s>>>(f, n_ptr, cap, tile_sums);
-    scan_tiles_k<T><<<1, kScanThreads, 0, s>>>(tile_sums, nt, total);
-    scan_down_k<F, T><<<nt, kScanThreads, 0, s>>>(f, n_ptr, cap, tile_sums, out);
+    launch_pdl(scan_reduce_k<F, T>, dim3(nt), dim3(kScanThreads), 0, s, f, n_ptr, cap, tile_sums);
+    launch_pdl(scan_tiles_k<T>, dim3(1), dim3(kScanThreads), 0, s, tile_sums, nt, total);
+    launch_pdl(scan_down_k<F, T>, dim3(nt), dim3(kScanThreads), 0, s, f, n_ptr, cap, tile_sums, out);
     note_launches(3);
 }
 

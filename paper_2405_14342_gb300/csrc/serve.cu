@@ -42,6 +42,7 @@ struct PackArg {
 __global__ void __launch_bounds__(256) serve_pack_k(PackArg pa, int n_req, long long total_pix, int C,
                                                     const float* __restrict__ out, const float* __restrict__ pix_T,
                                                     unsigned char* __restrict__ packed) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total_pix;
          p += (long long)gridDim.x * blockDim.x) {
         int lo = 0, hi = n_req - 1;
@@ -321,7 +322,7 @@ struct rogs_server {
             }
             long long blocks = (pix + 255) / 256;
             if (blocks > 152 * 8) blocks = 152 * 8;
-            serve_pack_k<<<(int)(blocks > 0 ? blocks : 1), 256, 0, s>>>(
+            launch_pdl(serve_pack_k, dim3((int)(blocks > 0 ? blocks : 1)), dim3(256), 0, s,
                 pa, (int)cams.size(), pix, C, out, reinterpret_cast<const float*>((char*)state + L.pix_T), packed);
             note_launches(1);
             doff = 0;

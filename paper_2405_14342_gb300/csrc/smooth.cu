@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_k(const int32_t* __rest
                                                             const float* __restrict__ xyz, float lambda,
                                                             float* __restrict__ grad_xyz,
                                                             float* __restrict__ partials) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ float sh[kSmoothThreads / 32];
     const long long cells = (long long)W * H;
     float acc = 0.0f;
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(kSmoothThreads) smooth_k(const int32_t* __rest
 
 // loss[0] = lambda / 4 * (sum of the partials), 32 lanes in a fixed order.
 __global__ void smooth_final_k(const float* __restrict__ partials, int n, float lambda, float* __restrict__ loss) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     float s = 0.0f;
     for (int i = threadIdx.x; i < n; i += 32) s += partials[i];
 #pragma unroll
@@ -74,8 +76,8 @@ void smooth_loss(const int32_t* grid_index, int grid_w, int grid_h, const float*
     long long nb = (cells + kSmoothThreads - 1) / kSmoothThreads;
     if (nb > smooth_blocks()) nb = smooth_blocks();
     if (nb < 1) nb = 1;
-    smooth_k<<<(int)nb, kSmoothThreads, 0, s>>>(grid_index, grid_w, grid_h, xyz, lambda, grad_xyz, partials);
-    smooth_final_k<<<1, 32, 0, s>>>(partials, (int)nb, lambda, loss);
+    launch_pdl(smooth_k, dim3((int)nb), dim3(kSmoothThreads), 0, s, grid_index, grid_w, grid_h, xyz, lambda, grad_xyz, partials);
+    launch_pdl(smooth_final_k, dim3(1), dim3(32), 0, s, partials, (int)nb, lambda, loss);
     note_launches(2);
 }
 

@@ -30,6 +30,7 @@ template <int IPT>
 __global__ void __launch_bounds__(kRsThreads) rs_upsweep_k(const uint32_t* __restrict__ keys,
                                                             const unsigned long long* n_ptr, unsigned long long cap,
                                                             int shift, uint32_t mask, uint32_t* __restrict__ hist) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     constexpr int kRsWarpItems = 32 * IPT;
     constexpr int kRsTile = kRsThreads * IPT;
     __shared__ uint32_t sh[kRsWarps][256];
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_k(const uint32_t* __res
 __global__ void __launch_bounds__(kScanThreads) rs_rowscan_k(uint32_t* __restrict__ hist,
                                                               const unsigned long long* n_ptr, unsigned long long cap,
                                                               int tile_keys, uint32_t* __restrict__ row_total) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ uint32_t sh[33];
     const unsigned long long n = rs_len(n_ptr, cap);
     const unsigned ntiles = (unsigned)((n + tile_keys - 1) / tile_keys);
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __r
                                                               const unsigned long long* n_ptr, unsigned long long cap,
                                                               int shift, uint32_t mask, const uint32_t* __restrict__ hist,
                                                               const uint32_t* __restrict__ row_total) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     constexpr int kRsWarpItems = 32 * IPT;
     constexpr int kRsTile = kRsThreads * IPT;
     __shared__ uint32_t digit_base[256];
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __r
 
 __global__ void copy_pairs_k(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
                              const unsigned long long* n_ptr, unsigned long long cap) {
+    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     const unsigned long long n = rs_len(n_ptr, cap);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
@@ -198,9 +202,9 @@ static void radix_passes(const uint32_t* kin, const uint32_t* vin, uint32_t* kou
         const int shift = 8 * p;
         const int bits = key_bits - shift < 8 ? key_bits - shift : 8;
         const uint32_t mask = (bits >= 32) ? 0xffffffffu : ((1u << bits) - 1u);
-        rs_upsweep_k<IPT><<<grid, kRsThreads, 0, s>>>(sk, n_ptr, cap, shift, mask, hist);
-        rs_rowscan_k<<<256, kScanThreads, 0, s>>>(hist, n_ptr, cap, tile_keys, row_total);
-        rs_downsweep_k<IPT><<<grid, kRsThreads, 0, s>>>(sk, sv, dk, dv, n_ptr, cap, shift, mask, hist, row_total);
+        launch_pdl(rs_upsweep_k<IPT>, dim3(grid), dim3(kRsThreads), 0, s, sk, n_ptr, cap, shift, mask, hist);
+        launch_pdl(rs_rowscan_k, dim3(256), dim3(kScanThreads), 0, s, hist, n_ptr, cap, tile_keys, row_total);
+        launch_pdl(rs_downsweep_k<IPT>, dim3(grid), dim3(kRsThreads), 0, s, sk, sv, dk, dv, n_ptr, cap, shift, mask, hist, row_total);
         note_launches(3);
         sk = dk;
         sv = dv;
@@ -214,7 +218,7 @@ void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
     if ((key_bits + 7) / 8 == 0) {
         unsigned long long blocks = (cap + 255) / 256;
         const int grid = (int)(blocks < 1 ? 1 : (blocks > 2048 ? 2048 : blocks));
-        copy_pairs_k<<<grid, 256, 0, s>>>(kin, vin, kout, vout, n_ptr, cap);
+        launch_pdl(copy_pairs_k, dim3(grid), dim3(256), 0, s, kin, vin, kout, vout, n_ptr, cap);
         note_launches(1);
         return;
     }
