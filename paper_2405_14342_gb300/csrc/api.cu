@@ -373,6 +373,7 @@ rogs_status rogs_create(const rogs_config* cfg, rogs_ctx** out) {
     }
     prepare_composite_fwd();
     prepare_composite_bwd();
+    prepare_sort();
     cudaDeviceSynchronize();
     *out = ctx;
     return ROGS_OK;

@@ -63,6 +63,7 @@ struct GradPtrs {
 
 // ---- sort.cu
 size_t radix_hist_words(unsigned long long cap);
+void prepare_sort();   // set the dynamic shared-memory limits (before any capture)
 void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t* kalt,
                       uint32_t* valt, const unsigned long long* n_ptr, unsigned long long cap, int key_bits,
                       uint32_t* hist, cudaStream_t s, int sort_tile = 4096);

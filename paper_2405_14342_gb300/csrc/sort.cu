@@ -42,11 +42,15 @@ __global__ void __launch_bounds__(kRsThreads) rs_upsweep_k(const uint32_t* __res
         for (int w = 0; w < kRsWarps; ++w) sh[w][threadIdx.x] = 0;
         __syncthreads();
         const unsigned long long base = (unsigned long long)tile * kRsTile + (unsigned long long)warp * kRsWarpItems;
-#pragma unroll 4
-        for (int k = 0; k < IPT; ++k) {
+        uint32_t key[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {   // every load in flight before the first count
             unsigned long long i = base + k * 32 + lane;
-            if (i < n) atomicAdd(&sh[warp][(keys[i] >> shift) & mask], 1u);
+            key[k] = i < n ? keys[i] : 0u;
         }
+#pragma unroll
+        for (int k = 0; k < IPT; ++k)
+            if (base + k * 32 + lane < n) atomicAdd(&sh[warp][(key[k] >> shift) & mask], 1u);
         __syncthreads();
         uint32_t s = 0;
 #pragma unroll
@@ -77,6 +81,24 @@ __global__ void __launch_bounds__(kScanThreads) rs_rowscan_k(uint32_t* __restric
     if (threadIdx.x == 0) row_total[blockIdx.x] = carry;
 }
 
+// Lanes of the warp (among `valid`) whose digit equals this lane's: one ballot
+// per digit bit, so the cost does not depend on how many distinct digits the
+// warp holds.
+__device__ __forceinline__ unsigned rs_peers(uint32_t d, uint32_t mask, unsigned valid) {
+    unsigned peers = valid;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if ((mask >> b) & 1u) {
+            const unsigned m = __ballot_sync(kFull, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? m : ~m;
+        }
+    }
+    return peers;
+}
+
+// Dynamic shared memory of rs_downsweep_k: the tile's keys and values in digit order.
+__host__ __device__ constexpr size_t rs_stage_bytes(int ipt) { return (size_t)2 * 4 * kRsThreads * ipt; }
+
 template <int IPT>
 __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __restrict__ kin,
                                                               const uint32_t* __restrict__ vin,
@@ -87,17 +109,22 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __r
     pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     constexpr int kRsWarpItems = 32 * IPT;
     constexpr int kRsTile = kRsThreads * IPT;
+    extern __shared__ uint32_t rs_stage[];   // [kRsTile] keys, then [kRsTile] values
     __shared__ uint32_t digit_base[256];
-    __shared__ uint32_t wh[kRsWarps][256];
+    __shared__ uint32_t wh[kRsWarps][256];   // per-warp digit counts, then per-warp tile-local starts
+    __shared__ uint32_t tile_start[256];     // tile-local start of each digit
+    __shared__ uint32_t out_base[256];       // global position of each digit's first key of the tile
     __shared__ uint32_t scan_w[kRsWarps + 1];
+    uint32_t* sk = rs_stage;
+    uint32_t* sv = rs_stage + kRsTile;
     const unsigned long long n = rs_len(n_ptr, cap);
     const unsigned ntiles = (unsigned)((n + kRsTile - 1) / kRsTile);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d0 = threadIdx.x;
     const unsigned lt = lanemask_lt();
 
-    // exclusive scan of the 256 digit totals
-    {
-        uint32_t v = row_total[threadIdx.x];
+    // block-wide exclusive scan of one value per thread (256 threads)
+    auto block_scan = [&](uint32_t v) -> uint32_t {
         uint32_t inc = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -111,56 +138,75 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __r
             for (int w = 0; w < kRsWarps; ++w) { uint32_t t = scan_w[w]; scan_w[w] = c; c += t; }
         }
         __syncthreads();
-        digit_base[threadIdx.x] = scan_w[warp] + inc - v;
+        const uint32_t r = scan_w[warp] + inc - v;
         __syncthreads();
-    }
+        return r;
+    };
+    // exclusive scan of the 256 digit totals
+    digit_base[d0] = block_scan(row_total[d0]);
 
     for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
 #pragma unroll
         for (int w = 0; w < kRsWarps; ++w) wh[w][threadIdx.x] = 0;
         __syncthreads();
         const unsigned long long base = (unsigned long long)tile * kRsTile + (unsigned long long)warp * kRsWarpItems;
+        const unsigned long long left = n - (unsigned long long)tile * kRsTile;
+        const int tile_n = (int)(left < (unsigned long long)kRsTile ? left : (unsigned long long)kRsTile);
         uint32_t key[IPT], val[IPT], rank[IPT];
 #pragma unroll
-        for (int k = 0; k < IPT; ++k) {
+        for (int k = 0; k < IPT; ++k) {   // every load in flight before the first rank
             unsigned long long i = base + k * 32 + lane;
-            bool valid = i < n;
-            key[k] = valid ? kin[i] : 0u;
-            val[k] = valid ? vin[i] : 0u;
-            unsigned vm = __ballot_sync(kFull, valid);
-            uint32_t d = (key[k] >> shift) & mask;
-            unsigned peers = 0;
+            key[k] = i < n ? kin[i] : 0u;
+            val[k] = i < n ? vin[i] : 0u;
+        }
+        // rank in key order: warp by warp, and inside a warp item row by item row,
+        // lanes below a lane first, so equal digits keep their input order
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const bool valid = base + k * 32 + lane < n;
+            const unsigned vm = __ballot_sync(kFull, valid);
+            const uint32_t d = (key[k] >> shift) & mask;
+            const unsigned peers = rs_peers(d, mask, vm);
             rank[k] = 0;
-            if (valid) {
-                peers = __match_any_sync(vm, d);
-                rank[k] = wh[warp][d] + __popc(peers & lt);
-            }
+            if (valid) rank[k] = wh[warp][d] + __popc(peers & lt);
             __syncwarp();
             if (valid && (peers & lt) == 0) wh[warp][d] += __popc(peers);
             __syncwarp();
         }
         __syncthreads();
         {
-            const int d = threadIdx.x;
-            uint32_t run = digit_base[d] + hist[(unsigned long long)d * ntiles + tile];
+            uint32_t cnt = 0;
 #pragma unroll
-            for (int w = 0; w < kRsWarps; ++w) {
-                uint32_t c = wh[w][d];
-                wh[w][d] = run;
-                run += c;
+            for (int w = 0; w < kRsWarps; ++w) {   // per-warp counts -> starts inside the digit's run
+                const uint32_t c = wh[w][d0];
+                wh[w][d0] = cnt;
+                cnt += c;
+            }
+            const uint32_t ts = block_scan(cnt);
+            tile_start[d0] = ts;
+            out_base[d0] = digit_base[d0] + hist[(unsigned long long)d0 * ntiles + tile];
+#pragma unroll
+            for (int w = 0; w < kRsWarps; ++w) wh[w][d0] += ts;
+        }
+        __syncthreads();
+        // keys into shared memory in digit order, then out in runs of equal digits
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            if (base + k * 32 + lane < n) {
+                const uint32_t d = (key[k] >> shift) & mask;
+                const uint32_t lp = wh[warp][d] + rank[k];
+                sk[lp] = key[k];
+                sv[lp] = val[k];
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < IPT; ++k) {
-            unsigned long long i = base + k * 32 + lane;
-            if (i < n) {
-                uint32_t d = (key[k] >> shift) & mask;
-                uint32_t pos = wh[warp][d] + rank[k];
-                if (rogs_ok(pos < n, 301u)) {
-                    kout[pos] = key[k];
-                    vout[pos] = val[k];
-                }
+        for (int j = threadIdx.x; j < tile_n; j += kRsThreads) {
+            const uint32_t kk = sk[j];
+            const uint32_t d = (kk >> shift) & mask;
+            const uint32_t pos = out_base[d] + (uint32_t)j - tile_start[d];
+            if (rogs_ok(pos < n, 301u)) {
+                kout[pos] = kk;
+                vout[pos] = sv[j];
             }
         }
         __syncthreads();
@@ -176,6 +222,12 @@ __global__ void copy_pairs_k(const uint32_t* kin, const uint32_t* vin, uint32_t*
         kout[i] = kin[i];
         vout[i] = vin[i];
     }
+}
+
+void prepare_sort() {
+    cudaFuncSetAttribute(rs_downsweep_k<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_stage_bytes(8));
+    cudaFuncSetAttribute(rs_downsweep_k<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_stage_bytes(16));
+    cudaFuncSetAttribute(rs_downsweep_k<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_stage_bytes(32));
 }
 
 size_t radix_hist_words(unsigned long long cap) {
@@ -204,7 +256,8 @@ static void radix_passes(const uint32_t* kin, const uint32_t* vin, uint32_t* kou
         const uint32_t mask = (bits >= 32) ? 0xffffffffu : ((1u << bits) - 1u);
         launch_pdl(rs_upsweep_k<IPT>, dim3(grid), dim3(kRsThreads), 0, s, sk, n_ptr, cap, shift, mask, hist);
         launch_pdl(rs_rowscan_k, dim3(256), dim3(kScanThreads), 0, s, hist, n_ptr, cap, tile_keys, row_total);
-        launch_pdl(rs_downsweep_k<IPT>, dim3(grid), dim3(kRsThreads), 0, s, sk, sv, dk, dv, n_ptr, cap, shift, mask, hist, row_total);
+        launch_pdl(rs_downsweep_k<IPT>, dim3(grid), dim3(kRsThreads), rs_stage_bytes(IPT), s, sk, sv, dk, dv, n_ptr, cap,
+                   shift, mask, hist, row_total);
         note_launches(3);
         sk = dk;
         sv = dv;
