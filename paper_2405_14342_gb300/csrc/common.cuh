@@ -238,6 +238,21 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Lanes of the warp (among `valid`) whose digit d (bits under `mask`, at most
+// 8) equals this lane's: one ballot per digit bit, so the cost does not depend
+// on how many distinct digits the warp holds.  Every lane must call it.
+__device__ __forceinline__ unsigned warp_digit_peers(uint32_t d, uint32_t mask, unsigned valid) {
+    unsigned peers = valid;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if ((mask >> b) & 1u) {
+            const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? m : ~m;
+        }
+    }
+    return peers;
+}
+
 // Binary search of the view owning global tile t (tile_base ascending).
 __device__ __forceinline__ int view_of_tile(const ViewParams* views, int n_views, long long t) {
     int lo = 0, hi = n_views - 1;

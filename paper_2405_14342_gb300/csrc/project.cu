@@ -6,13 +6,15 @@
 // supplementary's perspective box cull.
 //
 // Three launches, all over surfels with one thread per surfel looping over
-// the views (the surfel's 40 bytes of geometry are read once per frame for
-// every view):
+// the views:
 //   cull_k       visibility bitmask, one 32-bit word per (view, 32 surfels)
 //   scan         exclusive scan of the word popcounts, view-major
 //   project_k    the records of the visible (view, surfel) pairs, written in
 //                (view, surfel) order at their scanned positions, plus the
-//                depth sort keys.
+//                depth sort keys.  A warp first loads, lane = view, the
+//                visibility words and first positions of its 32 surfels in
+//                up to 32 views, then its surfels' inputs, then projects view
+//                by view.
 // The projection is evaluated again in project_k rather than carried from
 // cull_k; only cull_k's bit decides whether a record exists, so the two
 // evaluations never need to agree bit for bit.
@@ -27,14 +29,44 @@ struct ProjOut {
     int tx0, ty0, tx1, ty1;
 };
 
+// One surfel's inputs to the projection.  Position and opacity are loaded
+// once per surfel for all views; rotation and scales when a view first gets
+// past the cheap tests (box, near plane, opacity).
+struct SurfelIn {
+    float x, y, z, alpha;
+    float4 q;
+    float2 s;
+    bool has_shape;
+};
+
+__device__ __forceinline__ SurfelIn load_surfel_pos(const SurfelPtrs& sp, long long i) {
+    SurfelIn in;
+    in.x = sp.xyz[3 * i];
+    in.y = sp.xyz[3 * i + 1];
+    in.z = sp.xyz[3 * i + 2];
+    in.alpha = sp.opacity[i];
+    in.q = make_float4(0.f, 0.f, 0.f, 0.f);
+    in.s = make_float2(0.f, 0.f);
+    in.has_shape = false;
+    return in;
+}
+
+__device__ __forceinline__ void load_surfel_shape(const SurfelPtrs& sp, long long i, SurfelIn& in) {
+    if (in.has_shape) return;
+    in.q = reinterpret_cast<const float4*>(sp.quat)[i];
+    in.s = reinterpret_cast<const float2*>(sp.scale)[i];
+    in.has_shape = true;
+}
+
 __device__ __forceinline__ bool project_surfel(const ViewParams& v, const Consts& k, const SurfelPtrs& sp,
-                                               long long i, ProjOut& o) {
-    const float x = sp.xyz[3 * i], y = sp.xyz[3 * i + 1], z = sp.xyz[3 * i + 2];
+                                               long long i, SurfelIn& in, ProjOut& o) {
+    const float x = in.x, y = in.y, z = in.z;
     if (!box_keep(v, k, x, y)) return false;
     const float key = depth_key(v, x, y, z);
     if (v.kind == ROGS_PERSP && !(key > k.near_plane)) return false;
-    const float alpha = sp.opacity[i];
+    const float alpha = in.alpha;
     if (!(alpha >= k.alpha_min)) return false;
+    load_surfel_shape(sp, i, in);
 
     // camera-space centre p = R x + t, double-float (exact products)
     df p[3];
@@ -69,10 +101,10 @@ __device__ __forceinline__ bool project_surfel(const ViewParams& v, const Consts
     }
 
     // surfel axes: first two columns of R(q), q normalised
-    const float4 q = reinterpret_cast<const float4*>(sp.quat)[i];
+    const float4 q = in.q;
     const float qi = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     const float w = q.x * qi, qx = q.y * qi, qy = q.z * qi, qz = q.w * qi;
-    const float2 s = reinterpret_cast<const float2*>(sp.scale)[i];
+    const float2 s = in.s;
     const float c0x = (1.0f - 2.0f * (qy * qy + qz * qz)) * s.x;
     const float c0y = (2.0f * (qx * qy + w * qz)) * s.x;
     const float c0z = (2.0f * (qx * qz - w * qy)) * s.x;
@@ -142,8 +174,9 @@ __global__ void __launch_bounds__(kProjThreads) cull_k(const ViewParams* __restr
         for (int v = 0; v < n_views; ++v) {
             bool vis = false;
             if (i < sp.n) {
+                SurfelIn in = load_surfel_pos(sp, i);
                 ProjOut o;
-                vis = project_surfel(sv[v], k, sp, i, o);
+                vis = project_surfel(sv[v], k, sp, i, in, o);
             }
             const unsigned b = __ballot_sync(kFull, vis);
             if (lane == 0) bits[(long long)v * n_words + w] = b;
@@ -161,67 +194,86 @@ __global__ void __launch_bounds__(kProjThreads) project_k(const ViewParams* __re
     pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     extern __shared__ ViewParams sv[];
     load_views_smem(sv, views, n_views);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
+    const int C = k.C;
     const long long warps_total = (long long)gridDim.x * (kProjThreads / 32);
-    for (long long w = (long long)blockIdx.x * (kProjThreads / 32) + (threadIdx.x >> 5); w < n_words;
-         w += warps_total) {
+    for (long long w = (long long)blockIdx.x * (kProjThreads / 32) + wib; w < n_words; w += warps_total) {
         const long long i = w * 32 + lane;
-        for (int v = 0; v < n_views; ++v) {
-            const long long q = (long long)v * n_words + w;
-            const uint32_t b = bits[q];
-            if (!(b & (1u << lane))) continue;
-            const unsigned long long pos = (unsigned long long)word_off[q] + __popc(b & lt);
-            if (pos >= rec_cap) continue;
-            ProjOut o;
-            o.tx0 = o.ty0 = 1;
-            o.tx1 = o.ty1 = 0;
-            if (!project_surfel(sv[v], k, sp, i, o)) {
-                // cannot happen with identical arithmetic; keep the record inert
-                o.tx0 = o.ty0 = 1;
-                o.tx1 = o.ty1 = 0;
+        SurfelIn in{};
+        bool loaded = false;
+        for (int g = 0; g < n_views; g += 32) {
+            // lane = view: the visibility word and first record position of (view, w)
+            const int lv = g + lane;
+            const long long qv = (long long)lv * n_words + w;
+            const uint32_t bw = lv < n_views ? bits[qv] : 0u;
+            const uint32_t ow = bw ? word_off[qv] : 0u;
+            const unsigned anyv = __ballot_sync(kFull, bw != 0u);
+            if (!anyv) continue;
+            bool mine = false;   // some view of this group sees this lane's surfel
+            for (unsigned m = anyv; m; m &= m - 1) mine |= (__shfl_sync(kFull, bw, __ffs(m) - 1) >> lane) & 1u;
+            if (mine && !loaded) {   // the surfel's inputs, once for all its views
+                in = load_surfel_pos(sp, i);
+                load_surfel_shape(sp, i, in);
+                loaded = true;
             }
-            Record r;
-            float mi = floorf(o.mx.hi), ni = floorf(o.my.hi);
-            float mf = __fadd_rn(__fsub_rn(o.mx.hi, mi), o.mx.lo);
-            float nf = __fadd_rn(__fsub_rn(o.my.hi, ni), o.my.lo);
-            if (mf < 0.0f) { mi -= 1.0f; mf += 1.0f; } else if (mf >= 1.0f) { mi += 1.0f; mf -= 1.0f; }
-            if (nf < 0.0f) { ni -= 1.0f; nf += 1.0f; } else if (nf >= 1.0f) { ni += 1.0f; nf -= 1.0f; }
-            r.mxi = mi; r.myi = ni; r.mxf = mf; r.myf = nf;
-            r.ca = o.A; r.cb = o.B; r.cc = o.C; r.opacity = o.alpha;
-            r.depth = o.depth; r.key = o.key;
-            r.surfel = (uint32_t)i;
-            r.view = (uint32_t)v;
-            float4* dst = reinterpret_cast<float4*>(recs + pos);
-            const float4* src = reinterpret_cast<const float4*>(&r);
-            dst[0] = src[0];
-            dst[1] = src[1];
-            dst[2] = src[2];
-            uint2 rc;
-            if (o.tx1 >= o.tx0 && o.ty1 >= o.ty0) {
-                rc.x = (uint32_t)o.tx0 | ((uint32_t)o.ty0 << 16);
-                rc.y = (uint32_t)o.tx1 | ((uint32_t)o.ty1 << 16);
-            } else {
-                rc.x = 1u | (1u << 16);  // empty: x1 < x0
-                rc.y = 0u;
-            }
-            rects[pos] = rc;
-            keys[pos] = float_sort_bits(o.key);
-            vals[pos] = (uint32_t)pos;
-            // feature row: rgb, the C logits, depth, zeros
-            {
-                const int C = k.C;
-                const float* rgb = sp.rgb + 3ull * (unsigned long long)i;
-                const float* sem = sp.sem + (unsigned long long)C * (unsigned long long)i;
-                float4* fr = reinterpret_cast<float4*>(feat + pos * (unsigned long long)ncp);
-                for (int q = 0; q < ncp / 4; ++q) {
-                    float e[4];
-#pragma unroll
-                    for (int c4 = 0; c4 < 4; ++c4) {
-                        const int ch = 4 * q + c4;
-                        e[c4] = ch < 3 ? rgb[ch] : (ch - 3 < C ? sem[ch - 3] : (ch - 3 == C ? o.depth : 0.0f));
+            for (unsigned m = anyv; m; m &= m - 1) {
+                const int vv = __ffs(m) - 1;
+                const int v = g + vv;
+                const uint32_t b = __shfl_sync(kFull, bw, vv);
+                const uint32_t first = __shfl_sync(kFull, ow, vv);
+                const bool vis = (b >> lane) & 1u;
+                const uint32_t slot = __popc(b & lt);
+                const unsigned long long pos = (unsigned long long)first + slot;
+                if (vis && pos < rec_cap) {
+                    ProjOut o;
+                    o.tx0 = o.ty0 = 1;
+                    o.tx1 = o.ty1 = 0;
+                    if (!project_surfel(sv[v], k, sp, i, in, o)) {
+                        // cannot happen with identical arithmetic; keep the record inert
+                        o.tx0 = o.ty0 = 1;
+                        o.tx1 = o.ty1 = 0;
                     }
-                    fr[q] = make_float4(e[0], e[1], e[2], e[3]);
+                    Record r;
+                    float mi = floorf(o.mx.hi), ni = floorf(o.my.hi);
+                    float mf = __fadd_rn(__fsub_rn(o.mx.hi, mi), o.mx.lo);
+                    float nf = __fadd_rn(__fsub_rn(o.my.hi, ni), o.my.lo);
+                    if (mf < 0.0f) { mi -= 1.0f; mf += 1.0f; } else if (mf >= 1.0f) { mi += 1.0f; mf -= 1.0f; }
+                    if (nf < 0.0f) { ni -= 1.0f; nf += 1.0f; } else if (nf >= 1.0f) { ni += 1.0f; nf -= 1.0f; }
+                    r.mxi = mi; r.myi = ni; r.mxf = mf; r.myf = nf;
+                    r.ca = o.A; r.cb = o.B; r.cc = o.C; r.opacity = o.alpha;
+                    r.depth = o.depth; r.key = o.key;
+                    r.surfel = (uint32_t)i;
+                    r.view = (uint32_t)v;
+                    float4* dst = reinterpret_cast<float4*>(recs + pos);
+                    const float4* src = reinterpret_cast<const float4*>(&r);
+                    dst[0] = src[0];
+                    dst[1] = src[1];
+                    dst[2] = src[2];
+                    uint2 rc;
+                    if (o.tx1 >= o.tx0 && o.ty1 >= o.ty0) {
+                        rc.x = (uint32_t)o.tx0 | ((uint32_t)o.ty0 << 16);
+                        rc.y = (uint32_t)o.tx1 | ((uint32_t)o.ty1 << 16);
+                    } else {
+                        rc.x = 1u | (1u << 16);  // empty: x1 < x0
+                        rc.y = 0u;
+                    }
+                    rects[pos] = rc;
+                    keys[pos] = float_sort_bits(o.key);
+                    vals[pos] = (uint32_t)pos;
+                    // feature row: rgb, the C logits, depth, zeros
+                    const float* rgb = sp.rgb + 3ull * (unsigned long long)i;
+                    const float* sem = sp.sem + (unsigned long long)C * (unsigned long long)i;
+                    float4* fr = reinterpret_cast<float4*>(feat + pos * (unsigned long long)ncp);
+                    for (int q4 = 0; q4 < ncp / 4; ++q4) {
+                        float e[4];
+#pragma unroll
+                        for (int c4 = 0; c4 < 4; ++c4) {
+                            const int ch = 4 * q4 + c4;
+                            e[c4] = ch < 3 ? rgb[ch] : (ch - 3 < C ? sem[ch - 3] : (ch - 3 == C ? o.depth : 0.0f));
+                        }
+                        fr[q4] = make_float4(e[0], e[1], e[2], e[3]);
+                    }
                 }
             }
         }

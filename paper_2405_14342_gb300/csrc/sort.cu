@@ -81,21 +81,6 @@ __global__ void __launch_bounds__(kScanThreads) rs_rowscan_k(uint32_t* __restric
     if (threadIdx.x == 0) row_total[blockIdx.x] = carry;
 }
 
-// Lanes of the warp (among `valid`) whose digit equals this lane's: one ballot
-// per digit bit, so the cost does not depend on how many distinct digits the
-// warp holds.
-__device__ __forceinline__ unsigned rs_peers(uint32_t d, uint32_t mask, unsigned valid) {
-    unsigned peers = valid;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        if ((mask >> b) & 1u) {
-            const unsigned m = __ballot_sync(kFull, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? m : ~m;
-        }
-    }
-    return peers;
-}
-
 // Dynamic shared memory of rs_downsweep_k: the tile's keys and values in digit order.
 __host__ __device__ constexpr size_t rs_stage_bytes(int ipt) { return (size_t)2 * 4 * kRsThreads * ipt; }
 
@@ -166,7 +151,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_downsweep_k(const uint32_t* __r
             const bool valid = base + k * 32 + lane < n;
             const unsigned vm = __ballot_sync(kFull, valid);
             const uint32_t d = (key[k] >> shift) & mask;
-            const unsigned peers = rs_peers(d, mask, vm);
+            const unsigned peers = warp_digit_peers(d, mask, vm);
             rank[k] = 0;
             if (valid) rank[k] = wh[warp][d] + __popc(peers & lt);
             __syncwarp();
