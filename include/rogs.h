@@ -218,7 +218,10 @@ rogs_status rogs_init_from_poses(rogs_ctx* ctx, const float* grid_xy, int64_t n,
    cams: HOST [n_views]; exposure_ab: device [n_exposure,2] (a, b);
    out: device float[out_elems] (rogs_state_layout_of); state: device buffer
    of layout.total_bytes, 256-byte aligned, written here and read by
-   rogs_render_bwd.  ROGS_ERR_INVALID for n_views outside [1, ROGS_MAX_VIEWS],
+   rogs_render_bwd; the layout is that of rogs_state_layout_of for this
+   context and these cameras (its sections follow the context's capacities,
+   so a state laid out for another context may be too small: the library
+   cannot check this).  ROGS_ERR_INVALID for n_views outside [1, ROGS_MAX_VIEWS],
    a camera with non-positive size or focal length, or an exposure index
    outside [0, n_exposure). */
 rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,

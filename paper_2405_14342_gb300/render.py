@@ -59,6 +59,7 @@ class Frame:
     state: torch.Tensor     # uint8[layout.total_bytes]
     pix_base: List[int]
     generation: int = 0     # forwards run on this frame (its state belongs to the latest)
+    owner: int = 0          # id() of the Renderer whose context laid the state out
 
     def view(self, v: int, C: int) -> torch.Tensor:
         """Planes [3+C+1, H, W] of view v."""
@@ -124,21 +125,31 @@ class Renderer:
         for c in cams:
             pix.append(acc)
             acc += c.width * c.height
-        return Frame(list(cams), arr, L, out, state, pix)
+        return Frame(list(cams), arr, L, out, state, pix, owner=id(self))
+
+    def _own(self, frame: Frame) -> Frame:
+        # the state's section offsets follow this context's capacities: a frame
+        # laid out by another context may be too small for them
+        if frame.owner != id(self):
+            raise ValueError("frame was made by another Renderer; make it with this renderer's frame()")
+        return frame
 
     # -- the C-ABI calls --------------------------------------------------
 
     def forward(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, stream=None) -> Frame:
+        self._own(frame)
         frame.generation += 1
         R.rogs_render_fwd(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
                           frame.state, stream)
         return frame
 
     def counts(self, frame: Frame, stream=None, check=True) -> R.rogs_counts:
+        self._own(frame)
         return R.rogs_state_counts(self.ctx, frame.state, stream, check=check)
 
     def loss(self, frame: Frame, tgt_rgb, label, mask, lambda_c=1.0, lambda_s=0.06, loss=None, grad_out=None,
              stream=None):
+        self._own(frame)
         if loss is None:
             loss = torch.empty(1, dtype=torch.float32, device=self.device)
         if grad_out is None:
@@ -149,6 +160,7 @@ class Renderer:
 
     def backward(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, grad_out: torch.Tensor,
                  grads: Optional[dict] = None, stream=None) -> dict:
+        self._own(frame)
         if grads is None:
             grads = zero_grads(m, exposure)
         R.rogs_render_bwd(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.state,
@@ -167,6 +179,7 @@ class Renderer:
         """Forward, masked L1 + CE loss and backward with the loss fused into the
         backward kernel (rogs_train_step), plus lambda_smooth L_smooth when
         nonzero; gradients are added into `grads`."""
+        self._own(frame)
         frame.generation += 1
         R.rogs_train_step(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out, frame.state,
                           tgt_rgb, label, mask, lambda_c, lambda_s, loss, self.grads_struct(grads), stream,
@@ -177,6 +190,7 @@ class Renderer:
                     lambda_smooth=0.0) -> "Graph":
         """Capture rogs_train_step of `frame` into a CUDA graph (all pointers
         fixed; `stream` must be a non-default stream)."""
+        self._own(frame)
         g = R.rogs_train_graph_create(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
                                       frame.state, tgt_rgb, label, mask, lambda_c, lambda_s, loss,
                                       self.grads_struct(grads), stream, lambda_smooth)
@@ -210,6 +224,7 @@ class Renderer:
         return loss
 
     def render_graph(self, m: SurfelTensors, frame: Frame, exposure: torch.Tensor, stream=None) -> "Graph":
+        self._own(frame)
         g = R.rogs_render_graph_create(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out,
                                        frame.state, stream)
         return Graph(g, keep=(m, frame, exposure))

@@ -326,11 +326,15 @@ def test_capacity_overflow_is_reported(R):
     assert ei.value.status == rogs.ROGS_ERR_CAPACITY
     c = rr.counts(fr, check=False)
     assert c.need_records > 500 and c.n_records == 500 and c.status & 1
-    # a context with room renders the same frame fine afterwards
+    # a context with room renders the same cameras fine afterwards, in a frame
+    # laid out for its own capacities (the small context's frame is refused)
     rr2 = make(R, m.num_classes)
-    rr2.forward(st, fr, torch.zeros(1, 2, device="cuda"))
+    with pytest.raises(ValueError, match="another Renderer"):
+        rr2.forward(st, fr, torch.zeros(1, 2, device="cuda"))
+    fr2 = rr2.frame([scenes.tiny_camera()])
+    rr2.forward(st, fr2, torch.zeros(1, 2, device="cuda"))
     torch.cuda.synchronize()
-    assert rr2.counts(fr).status == 0
+    assert rr2.counts(fr2).status == 0
 
 
 def test_invalid_arguments_are_rejected(R):
