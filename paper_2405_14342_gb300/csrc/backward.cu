@@ -347,7 +347,15 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             float acc[NCP];
 #pragma unroll
             for (int ch = 0; ch < NCP; ++ch) acc[ch] = 0.0f;
-            float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, g3 = 0.0f, g4 = 0.0f, g5 = 0.0f;
+            // The conic and mean gradients need sums over the pixels of dp times
+            // (1, dx, dy, dx^2, dx dy, dy^2), with (dx, dy) the pixel's offset
+            // from the mean.  Written as (dxc + ux, dyc + uy), with (ux, uy) the
+            // pixel's offset from the block centre (a half-integer constant per
+            // pixel) and (dxc, dyc) the centre's offset from the mean, they
+            // follow from six moments of dp over (ux, uy), expanded once per
+            // entry after the loop.
+            constexpr float hx = 0.5f * (float)(BW - 1), hy = 0.5f * (float)(BH - 1);
+            float m0 = 0.0f, mx = 0.0f, my = 0.0f, mxx = 0.0f, mxy = 0.0f, myy = 0.0f;
             for (unsigned q = pmask; q;) {
                 const int p1 = __ffs(q) - 1;
                 q &= q - 1;
@@ -368,19 +376,30 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
                     acc[4 * k4 + 2] = fmaf(w2, a2.z, fmaf(w1, a1.z, acc[4 * k4 + 2]));
                     acc[4 * k4 + 3] = fmaf(w2, a2.w, fmaf(w1, a1.w, acc[4 * k4 + 3]));
                 }
-                const float ax = dx0 + (float)(p1 % BW), ay = dy0 + (float)(p1 / BW);
-                const float bxo = dx0 + (float)(p2 % BW), byo = dy0 + (float)(p2 / BW);
-                g0 = fmaf(dp1, cc.x * ax + cc.y * ay, fmaf(dp2, cc.x * bxo + cc.y * byo, g0));
-                g1 = fmaf(dp1, cc.y * ax + cc.z * ay, fmaf(dp2, cc.y * bxo + cc.z * byo, g1));
-                g2 = fmaf(-0.5f * dp1, ax * ax, fmaf(-0.5f * dp2, bxo * bxo, g2));
-                g3 = fmaf(-dp1, ax * ay, fmaf(-dp2, bxo * byo, g3));
-                g4 = fmaf(-0.5f * dp1, ay * ay, fmaf(-0.5f * dp2, byo * byo, g4));
-                g5 += dp1 + dp2;
+                const float ux1 = (float)(p1 % BW) - hx, uy1 = (float)(p1 / BW) - hy;
+                const float ux2 = (float)(p2 % BW) - hx, uy2 = (float)(p2 / BW) - hy;
+                m0 += dp1 + dp2;
+                mx = fmaf(dp1, ux1, fmaf(dp2, ux2, mx));
+                my = fmaf(dp1, uy1, fmaf(dp2, uy2, my));
+                const float ex1 = dp1 * ux1, ex2 = dp2 * ux2;
+                mxx = fmaf(ex1, ux1, fmaf(ex2, ux2, mxx));
+                mxy = fmaf(ex1, uy1, fmaf(ex2, uy2, mxy));
+                myy = fmaf(dp1 * uy1, uy1, fmaf(dp2 * uy2, uy2, myy));
             }
             if (any) {   // the entry's row of the tables becomes its gradient row
+                const float dxc = dx0 + hx, dyc = dy0 + hy;
+                const float sx = fmaf(dxc, m0, mx), sy = fmaf(dyc, m0, my);   // sum dp dx, sum dp dy
+                const float sxx = fmaf(dxc, fmaf(dxc, m0, 2.0f * mx), mxx);     // sum dp dx^2
+                const float sxy = fmaf(dxc, fmaf(dyc, m0, my), fmaf(dyc, mx, mxy));   // sum dp dx dy
+                const float syy = fmaf(dyc, fmaf(dyc, m0, 2.0f * my), myy);     // sum dp dy^2
                 float* r0 = s_w + e * SP;
                 float* r1 = s_p + e * SP;
-                r0[0] = g0; r0[1] = g1; r0[2] = g2; r0[3] = g3; r0[4] = g4; r0[5] = g5 / cc.w;
+                r0[0] = fmaf(cc.x, sx, cc.y * sy);
+                r0[1] = fmaf(cc.y, sx, cc.z * sy);
+                r0[2] = -0.5f * sxx;
+                r0[3] = -sxy;
+                r0[4] = -0.5f * syy;
+                r0[5] = m0 / cc.w;
                 // the padded channels are zero and never flushed; the widest rows
                 // (6 + 64 > 2 * SP) keep only the real ones, the others write all
 #pragma unroll
