@@ -134,9 +134,11 @@ typedef struct {
                  its C logits, the record's depth, then zeros; NCP = 3 + C + 1
                  rounded up to 8, 16, 24, 32 or 64 (what the compositing
                  kernels stage per list entry, one aligned row per record)
-     pair_mc     float[8] per pair, in pair_rec order: the first 32 bytes of
-                 its record (mean_int, mean_frac, conic, alpha), so that a
-                 list walk reads them without going through the record id
+     pair_mc     float[8] per pair, in pair_rec order: its record's
+                 mean_int, mean_frac, the conic scaled for a base-2
+                 exponential (-A/2 log2 e, -B log2 e, -C/2 log2 e) and
+                 alpha, so that a list walk reads them without going
+                 through the record id
      pair_blk    uint8 per pair: bit w set iff the record's footprint can
                  reach the w-th pixel block of its tile (the 32-pixel block
                  of one compositing warp: 16x2 in 16x16 tiles, 8x4 in 8x8

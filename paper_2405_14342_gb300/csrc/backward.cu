@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         if (lane < h) {
             const int e = lane;
             const float4 mm = s_m[e];
-            const float4 cc = s_c[e];
+            const float4 cc = conic_from_exp2(s_c[e]);   // (A, B, C, alpha)
             // pixel offsets relative to the block's first pixel centre
             const float dx0 = pix_offset((float)bx + 0.5f, mm.x, mm.z);
             const float dy0 = pix_offset((float)by + 0.5f, mm.y, mm.w);

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict_
         const float4* r4 = reinterpret_cast<const float4*>(&rec);
         const float4 m = r4[0], c = r4[1];
         pair_mc[2 * p] = m;
-        pair_mc[2 * p + 1] = c;
+        pair_mc[2 * p + 1] = conic_to_exp2(c);   // the form the list walks evaluate
         const ViewParams& v = views[rec.view];   // the tile is in the record's view
         const long long lt = (long long)t - v.tile_base;
         const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);

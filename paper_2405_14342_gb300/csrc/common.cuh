@@ -192,13 +192,30 @@ __device__ __forceinline__ float pix_offset(float pc, float mi, float mf) {
 }
 
 // Per-pixel opacity a = min(alpha_max, alpha * exp(power)) with
-// power = -0.5 (A dx^2 + 2 B dx dy + C dy^2).  Written with explicit fused
-// operations so that the forward and the backward kernels evaluate it
-// bit-identically.  Returns a; g receives exp(power).
-__device__ __forceinline__ float surfel_alpha(float dx, float dy, float A, float B, float C, float alpha,
+// power = -0.5 (A dx^2 + 2 B dx dy + C dy^2), evaluated as a base-2
+// exponential of the same quadratic form with the conic pre-scaled once per
+// pair (conic_to_exp2): A2 = -A/2 log2 e, B2 = -B log2 e, C2 = -C/2 log2 e,
+// so exp(power) = 2^(A2 dx^2 + B2 dx dy + C2 dy^2) takes five multiplies and
+// multiply-adds and one ex2.  Written with explicit rounding so that the forward and the
+// backward kernels evaluate it bit-identically.  Returns a; g receives
+// exp(power).
+constexpr float kLog2e = 1.4426950408889634f;
+__host__ __device__ __forceinline__ float4 conic_to_exp2(float4 c) {   // (A, B, C, alpha) -> (A2, B2, C2, alpha)
+    return make_float4(c.x * (-0.5f * kLog2e), c.y * -kLog2e, c.z * (-0.5f * kLog2e), c.w);
+}
+__host__ __device__ __forceinline__ float4 conic_from_exp2(float4 c) {   // back to (A, B, C, alpha), up to rounding
+    return make_float4(c.x * (-2.0f / kLog2e), c.y * (-1.0f / kLog2e), c.z * (-2.0f / kLog2e), c.w);
+}
+__device__ __forceinline__ float exp2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float surfel_alpha(float dx, float dy, float A2, float B2, float C2, float alpha,
                                               float alpha_max, float& g) {
-    float q = __fmaf_rn(__fmul_rn(A, dx), dx, __fmaf_rn(__fmul_rn(C, dy), dy, __fmul_rn(__fmul_rn(2.0f, B), __fmul_rn(dx, dy))));
-    g = __expf(__fmul_rn(-0.5f, q));
+    // q = (A2 dx + B2 dy) dx + (C2 dy) dy
+    const float q = __fmaf_rn(__fmaf_rn(A2, dx, __fmul_rn(B2, dy)), dx, __fmul_rn(__fmul_rn(C2, dy), dy));
+    g = exp2_approx(q);
     return fminf(alpha_max, __fmul_rn(alpha, g));
 }
 
