@@ -335,15 +335,16 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             reinterpret_cast<float4*>(s_G + lane * NCP)[q] = make_float4(G[4 * q], G[4 * q + 1], G[4 * q + 2], G[4 * q + 3]);
         __syncwarp();
         // phase B (lane = entry): sum the entry's gradient over the pixels that got
-        // anything, two pixels per step and without branches (w = 0 adds nothing)
+        // anything, two pixels per step and without branches (w = 0 adds nothing).
+        // With h <= 16 (8) entries the warp splits into 2 (4) groups of E lanes,
+        // group g taking the g-th quarter or half of the pixels, and the groups'
+        // sums are added with shuffles: fewer pixel steps for short chunks.
         bool any = false;
-        if (lane < h) {
-            const int e = lane;
-            const float4 mm = s_m[e];
-            const float4 cc = conic_from_exp2(s_c[e]);   // (A, B, C, alpha)
-            // pixel offsets relative to the block's first pixel centre
-            const float dx0 = pix_offset((float)bx + 0.5f, mm.x, mm.z);
-            const float dy0 = pix_offset((float)by + 0.5f, mm.y, mm.w);
+        {
+            const int E = h <= 8 ? 8 : (h <= 16 ? 16 : 32);   // lanes per group (h is warp-uniform)
+            const int e = lane & (E - 1), grp = lane / E;
+            const bool act = e < h;
+            const unsigned gmask = E == 32 ? kFull : (((1u << E) - 1u) << (grp * E));
             float acc[NCP];
 #pragma unroll
             for (int ch = 0; ch < NCP; ++ch) acc[ch] = 0.0f;
@@ -356,37 +357,56 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             // entry after the loop.
             constexpr float hx = 0.5f * (float)(BW - 1), hy = 0.5f * (float)(BH - 1);
             float m0 = 0.0f, mx = 0.0f, my = 0.0f, mxx = 0.0f, mxy = 0.0f, myy = 0.0f;
-            for (unsigned q = pmask; q;) {
-                const int p1 = __ffs(q) - 1;
-                q &= q - 1;
-                const int p2 = q ? __ffs(q) - 1 : p1;
-                const float w1 = s_w[e * SP + p1];
-                const float w2 = q ? s_w[e * SP + p2] : 0.0f;
-                const float dp1 = s_p[e * SP + p1];
-                const float dp2 = q ? s_p[e * SP + p2] : 0.0f;
-                q &= q - 1;
-                any |= (w1 != 0.0f) | (w2 != 0.0f);
-                const float4* r1 = reinterpret_cast<const float4*>(s_G + p1 * NCP);
-                const float4* r2 = reinterpret_cast<const float4*>(s_G + p2 * NCP);
+            if (act) {
+                for (unsigned q = pmask & gmask; q;) {
+                    const int p1 = __ffs(q) - 1;
+                    q &= q - 1;
+                    const int p2 = q ? __ffs(q) - 1 : p1;
+                    const float w1 = s_w[e * SP + p1];
+                    const float w2 = q ? s_w[e * SP + p2] : 0.0f;
+                    const float dp1 = s_p[e * SP + p1];
+                    const float dp2 = q ? s_p[e * SP + p2] : 0.0f;
+                    q &= q - 1;
+                    any |= (w1 != 0.0f) | (w2 != 0.0f);
+                    const float4* r1 = reinterpret_cast<const float4*>(s_G + p1 * NCP);
+                    const float4* r2 = reinterpret_cast<const float4*>(s_G + p2 * NCP);
 #pragma unroll
-                for (int k4 = 0; k4 < NCP / 4; ++k4) {
-                    const float4 a1 = r1[k4], a2 = r2[k4];
-                    acc[4 * k4] = fmaf(w2, a2.x, fmaf(w1, a1.x, acc[4 * k4]));
-                    acc[4 * k4 + 1] = fmaf(w2, a2.y, fmaf(w1, a1.y, acc[4 * k4 + 1]));
-                    acc[4 * k4 + 2] = fmaf(w2, a2.z, fmaf(w1, a1.z, acc[4 * k4 + 2]));
-                    acc[4 * k4 + 3] = fmaf(w2, a2.w, fmaf(w1, a1.w, acc[4 * k4 + 3]));
+                    for (int k4 = 0; k4 < NCP / 4; ++k4) {
+                        const float4 a1 = r1[k4], a2 = r2[k4];
+                        acc[4 * k4] = fmaf(w2, a2.x, fmaf(w1, a1.x, acc[4 * k4]));
+                        acc[4 * k4 + 1] = fmaf(w2, a2.y, fmaf(w1, a1.y, acc[4 * k4 + 1]));
+                        acc[4 * k4 + 2] = fmaf(w2, a2.z, fmaf(w1, a1.z, acc[4 * k4 + 2]));
+                        acc[4 * k4 + 3] = fmaf(w2, a2.w, fmaf(w1, a1.w, acc[4 * k4 + 3]));
+                    }
+                    const float ux1 = (float)(p1 % BW) - hx, uy1 = (float)(p1 / BW) - hy;
+                    const float ux2 = (float)(p2 % BW) - hx, uy2 = (float)(p2 / BW) - hy;
+                    m0 += dp1 + dp2;
+                    mx = fmaf(dp1, ux1, fmaf(dp2, ux2, mx));
+                    my = fmaf(dp1, uy1, fmaf(dp2, uy2, my));
+                    const float ex1 = dp1 * ux1, ex2 = dp2 * ux2;
+                    mxx = fmaf(ex1, ux1, fmaf(ex2, ux2, mxx));
+                    mxy = fmaf(ex1, uy1, fmaf(ex2, uy2, mxy));
+                    myy = fmaf(dp1 * uy1, uy1, fmaf(dp2 * uy2, uy2, myy));
                 }
-                const float ux1 = (float)(p1 % BW) - hx, uy1 = (float)(p1 / BW) - hy;
-                const float ux2 = (float)(p2 % BW) - hx, uy2 = (float)(p2 / BW) - hy;
-                m0 += dp1 + dp2;
-                mx = fmaf(dp1, ux1, fmaf(dp2, ux2, mx));
-                my = fmaf(dp1, uy1, fmaf(dp2, uy2, my));
-                const float ex1 = dp1 * ux1, ex2 = dp2 * ux2;
-                mxx = fmaf(ex1, ux1, fmaf(ex2, ux2, mxx));
-                mxy = fmaf(ex1, uy1, fmaf(ex2, uy2, mxy));
-                myy = fmaf(dp1 * uy1, uy1, fmaf(dp2 * uy2, uy2, myy));
             }
+            for (int o = E; o < 32; o <<= 1) {   // add the groups' sums (all lanes)
+#pragma unroll
+                for (int ch = 0; ch < NCP; ++ch) acc[ch] += __shfl_xor_sync(kFull, acc[ch], o);
+                m0 += __shfl_xor_sync(kFull, m0, o);
+                mx += __shfl_xor_sync(kFull, mx, o);
+                my += __shfl_xor_sync(kFull, my, o);
+                mxx += __shfl_xor_sync(kFull, mxx, o);
+                mxy += __shfl_xor_sync(kFull, mxy, o);
+                myy += __shfl_xor_sync(kFull, myy, o);
+                any = __shfl_xor_sync(kFull, (int)any, o) != 0 || any;
+            }
+            any = any && act && grp == 0;
             if (any) {   // the entry's row of the tables becomes its gradient row
+                const float4 mm = s_m[e];
+                const float4 cc = conic_from_exp2(s_c[e]);   // (A, B, C, alpha)
+                // offsets of the block's first pixel centre and of its centre from the mean
+                const float dx0 = pix_offset((float)bx + 0.5f, mm.x, mm.z);
+                const float dy0 = pix_offset((float)by + 0.5f, mm.y, mm.w);
                 const float dxc = dx0 + hx, dyc = dy0 + hy;
                 const float sx = fmaf(dxc, m0, mx), sy = fmaf(dyc, m0, my);   // sum dp dx, sum dp dy
                 const float sxx = fmaf(dxc, fmaf(dxc, m0, 2.0f * mx), mxx);     // sum dp dx^2
