@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     const int bx = tx * TW + (warp % WX) * BW, by = ty * TH + (warp / WX) * BH;
     const int px = bx + lane % BW, py = by + lane / BW;
     const bool inside = px < W && py < H;
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const int2 org = offset_origin(bx, by);   // the same for every pixel of the block
+    const float lx = (float)(px - org.x), ly = (float)(py - org.y);
     const uint2 trange = a.ranges[tile];
     const uint32_t start = trange.x;
     const int C = k.C;
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         mask_first = __ballot_sync(kFull, hit);
         if (hit) {
             const int slot = __popc(mask_first & lt_mask);
-            s_m[slot] = m;
+            s_m[slot] = block_offsets(m, org);
             s_c[slot] = c;
             s_rec[slot] = rec;
             stage_record_features_async<NCP>(s_f + slot * NCP, a.feat, rec);
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             mask = __ballot_sync(kFull, hit);
             if (hit) {
                 const int slot = __popc(mask & lt_mask);
-                s_m[slot] = m;
+                s_m[slot] = block_offsets(m, org);
                 s_c[slot] = c;
                 s_rec[slot] = rec;
                 stage_record_features<NCP>(s_f + slot * NCP, a.feat, rec);
@@ -296,8 +297,8 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         for (int jj = h - 1; jj >= 0; --jj) {
             const float4 mm = s_m[jj];
             const float4 cc = s_c[jj];
-            const float dx = pix_offset(pxc, mm.x, mm.z);
-            const float dy = pix_offset(pyc, mm.y, mm.w);
+            const float dx = __fadd_rn(mm.x, lx);
+            const float dy = __fadd_rn(mm.y, ly);
             float g;
             const float al = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, g);
             const bool valid = jj < kmax && al >= amin;
@@ -402,11 +403,9 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             }
             any = any && act && grp == 0;
             if (any) {   // the entry's row of the tables becomes its gradient row
-                const float4 mm = s_m[e];
+                const float4 mm = s_m[e];   // offsets of pixel org's centre from the mean
                 const float4 cc = conic_from_exp2(s_c[e]);   // (A, B, C, alpha)
-                // offsets of the block's first pixel centre and of its centre from the mean
-                const float dx0 = pix_offset((float)bx + 0.5f, mm.x, mm.z);
-                const float dy0 = pix_offset((float)by + 0.5f, mm.y, mm.w);
+                const float dx0 = mm.x + (float)(bx - org.x), dy0 = mm.y + (float)(by - org.y);   // block's first pixel
                 const float dxc = dx0 + hx, dyc = dy0 + hy;
                 const float sx = fmaf(dxc, m0, mx), sy = fmaf(dyc, m0, my);   // sum dp dx, sum dp dy
                 const float sxx = fmaf(dxc, fmaf(dxc, m0, 2.0f * mx), mxx);     // sum dp dx^2

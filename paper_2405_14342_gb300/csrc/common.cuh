@@ -191,6 +191,17 @@ __device__ __forceinline__ float pix_offset(float pc, float mi, float mf) {
     return __fsub_rn(__fsub_rn(pc, mi), mf);
 }
 
+// Offsets from a pair's split mean m (mean_int, mean_frac) of the centre of
+// pixel (x0, y0), staged once per entry and warp; pixel (x0 + lx, y0 + ly) is
+// then at (dx0 + lx, dy0 + ly), one add per axis (both compositing kernels
+// evaluate it this way).  The reference pixel is offset_origin(px, py): the
+// same for every pixel of any warp block shape, so the rounding, and with it
+// every output, does not depend on the tile shape.
+__device__ __forceinline__ int2 offset_origin(int px, int py) { return make_int2(px & ~31, py & ~3); }
+__device__ __forceinline__ float4 block_offsets(float4 m, int2 o) {
+    return make_float4(pix_offset((float)o.x + 0.5f, m.x, m.z), pix_offset((float)o.y + 0.5f, m.y, m.w), 0.0f, 0.0f);
+}
+
 // Per-pixel opacity a = min(alpha_max, alpha * exp(power)) with
 // power = -0.5 (A dx^2 + 2 B dx dy + C dy^2), evaluated as a base-2
 // exponential of the same quadratic form with the conic pre-scaled once per

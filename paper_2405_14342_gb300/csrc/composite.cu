@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
     const int bx = tx * TW + (warp % WX) * BW, by = ty * TH + (warp / WX) * BH;
     const int px = bx + lane % BW, py = by + lane / BW;
     const bool inside = px < W && py < H;
-    const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+    const int2 org = offset_origin(bx, by);   // the same for every pixel of the block
+    const float lx = (float)(px - org.x), ly = (float)(py - org.y);
     const uint2 rg = ranges[tile];
     const uint32_t start = rg.x, end = rg.y > rg.x ? rg.y : rg.x;
     const int C = k.C;
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
         const int h = __popc(mask);
         if (hit) {
             const int slot = __popc(mask & lt_mask);
-            s_m[slot] = m;
+            s_m[slot] = block_offsets(m, org);
             s_c[slot] = c;
             s_idx[slot] = j - start + 1;
             stage_record_features<NCP>(s_f + slot * NCP, feat, rec);
@@ -130,8 +131,8 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
         for (int jj = 0; jj < h; ++jj) {
             const float4 mm = s_m[jj];
             const float4 cc = s_c[jj];
-            const float dx = pix_offset(pxc, mm.x, mm.z);
-            const float dy = pix_offset(pyc, mm.y, mm.w);
+            const float dx = __fadd_rn(mm.x, lx);
+            const float dy = __fadd_rn(mm.y, ly);
             float gp;
             const float a = surfel_alpha(dx, dy, cc.x, cc.y, cc.z, cc.w, amax, gp);
             bool valid = !done && a >= amin;
