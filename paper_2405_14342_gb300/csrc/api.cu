@@ -583,7 +583,7 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
                          ctx->hist, s, cfg.sort_tile);
         prof_mark(ctx, 2, s);
         scan_pairs(ctx->dv_b, rects, hdr, rcap, ctx->pair_off, ctx->pair_tiles, hdr, pcap, s);
-        emit_pairs(views, ctx->dv_b, recs, rects, ctx->pair_off, hdr, rcap, ctx->pk_a, ctx->pv_a, pcap, s);
+        emit_pairs(views, n_views, ctx->dv_b, recs, rects, ctx->pair_off, hdr, rcap, ctx->pk_a, ctx->pv_a, pcap, s);
         // tile sort: stable on the global tile id; lists stay in depth order
         prof_mark(ctx, 3, s);
         radix_sort_pairs(ctx->pk_a, ctx->pv_a, ctx->pk_b, pair_rec, ctx->pk_c, ctx->pv_c, &hdr->n_pairs, pcap,

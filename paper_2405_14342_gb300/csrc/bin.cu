@@ -41,7 +41,18 @@ void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeade
     note_launches(1);
 }
 
-__global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict__ views,
+// The views' first tile ids and tile columns, staged in shared memory: the
+// per-entry kernels below read them once per list entry.
+__device__ __forceinline__ void load_tile_geometry(long long* s_base, int* s_cols, const ViewParams* views,
+                                                   int n_views) {
+    for (int v = threadIdx.x; v < n_views; v += blockDim.x) {
+        s_base[v] = views[v].tile_base;
+        s_cols[v] = views[v].tiles_x;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict__ views, int n_views,
                                                     const uint32_t* __restrict__ sorted_rec,
                                                     const Record* __restrict__ recs, const uint2* __restrict__ rects,
                                                     const unsigned long long* __restrict__ pair_off,
@@ -49,6 +60,9 @@ __global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict
                                                     uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals,
                                                     unsigned long long pair_cap) {
     pdl_wait();   // after the previous kernel of the stream (programmatic launch)
+    __shared__ long long s_base[kMaxViews];
+    __shared__ int s_cols[kMaxViews];
+    load_tile_geometry(s_base, s_cols, views, n_views);
     const unsigned long long n = scan_len(&hdr->n_records, rec_cap);
     for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
@@ -58,26 +72,28 @@ __global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict
         const int x0 = (int)(r.x & 0xffffu), y0 = (int)(r.x >> 16);
         const int x1 = (int)(r.y & 0xffffu), y1 = (int)(r.y >> 16);
         if (x1 < x0 || y1 < y0) continue;
-        const ViewParams& v = views[recs[rec].view];
+        const uint32_t vi = recs[rec].view;
+        if (!rogs_ok(vi < (uint32_t)n_views, 403u)) continue;
         unsigned long long p = pair_off[j];
-        const long long base = v.tile_base;
+        const long long base = s_base[vi];
+        const int cols = s_cols[vi];
         for (int ty = y0; ty <= y1; ++ty) {
             for (int tx = x0; tx <= x1; ++tx, ++p) {
                 if (p >= pair_cap) return;  // overflow: recorded by finalize_pairs_k
-                pair_keys[p] = (uint32_t)(base + (long long)ty * v.tiles_x + tx);
+                pair_keys[p] = (uint32_t)(base + (long long)ty * cols + tx);
                 pair_vals[p] = rec;
             }
         }
     }
 }
 
-void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Record* recs, const uint2* rects,
+void emit_pairs(const ViewParams* views, int n_views, const uint32_t* sorted_rec, const Record* recs, const uint2* rects,
                 const unsigned long long* pair_off, const StateHeader* hdr, unsigned long long rec_cap,
                 uint32_t* pair_keys, uint32_t* pair_vals, unsigned long long pair_cap, cudaStream_t s) {
     unsigned long long blocks = (rec_cap + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    launch_pdl(emit_pairs_k, dim3((int)blocks), dim3(256), 0, s, views, sorted_rec, recs, rects, pair_off, hdr, rec_cap, pair_keys,
+    launch_pdl(emit_pairs_k, dim3((int)blocks), dim3(256), 0, s, views, n_views, sorted_rec, recs, rects, pair_off, hdr, rec_cap, pair_keys,
                                               pair_vals, pair_cap);
     note_launches(1);
 }
@@ -90,28 +106,34 @@ __global__ void __launch_bounds__(256) tile_ranges_k(const uint32_t* __restrict_
                                                      uint2* __restrict__ ranges, float4* __restrict__ pair_mc,
                                                      uint8_t* __restrict__ pair_blk) {
     pdl_wait();   // after the previous kernel of the stream (programmatic launch)
+    __shared__ long long s_base[kMaxViews];
+    __shared__ int s_cols[kMaxViews];
+    load_tile_geometry(s_base, s_cols, views, n_views);
     const unsigned long long n = scan_len(&hdr->n_pairs, cap);
     const int bw = block_w(k.tile_w, k.tile_h), bh = 32 / bw;
-    const int wx = k.tile_w / bw, nw = k.tile_w * k.tile_h / 32;   // the warps' pixel blocks of a tile
+    const int wx = k.tile_w / bw, wy = k.tile_h / bh;   // the warps' pixel blocks of a tile: wx columns, wy rows
     for (unsigned long long p = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; p < n;
          p += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t t = keys[p];
         if (p == 0 || keys[p - 1] != t) ranges[t].x = (uint32_t)p;
         if (p + 1 == n || keys[p + 1] != t) ranges[t].y = (uint32_t)(p + 1);
         if (!rogs_ok(pair_rec[p] < k.rec_cap, 402u)) continue;
-        const Record& rec = recs[pair_rec[p]];
-        const float4* r4 = reinterpret_cast<const float4*>(&rec);
+        const float4* r4 = reinterpret_cast<const float4*>(recs + pair_rec[p]);
         const float4 m = r4[0], c = r4[1];
+        const uint32_t vi = __float_as_uint(r4[2].w);   // the record's view: the tile is in it
         pair_mc[2 * p] = m;
         pair_mc[2 * p + 1] = conic_to_exp2(c);   // the form the list walks evaluate
-        const ViewParams& v = views[rec.view];   // the tile is in the record's view
-        const long long lt = (long long)t - v.tile_base;
-        const int tx = (int)(lt % v.tiles_x), ty = (int)(lt / v.tiles_x);
+        if (!rogs_ok(vi < (uint32_t)n_views, 404u)) continue;
+        const uint32_t lt = (uint32_t)((long long)t - s_base[vi]);   // tile within its view (< 2^31)
+        const uint32_t cols = (uint32_t)s_cols[vi];
+        const uint32_t ty = lt / cols, tx = lt - ty * cols;
         const float2 r = block_cull_radii(c, k.alpha_min);
         uint32_t bm = 0;
-        for (int w = 0; w < nw; ++w) {
-            const int bx = tx * k.tile_w + (w % wx) * bw, by = ty * k.tile_h + (w / wx) * bh;
-            if (box_hits_block(m, r, (float)bx, (float)by, bw, bh)) bm |= 1u << w;
+        int w = 0;
+        for (int yb = 0; yb < wy; ++yb) {
+            const float by = (float)((int)ty * k.tile_h + yb * bh);
+            for (int xb = 0; xb < wx; ++xb, ++w)
+                if (box_hits_block(m, r, (float)((int)tx * k.tile_w + xb * bw), by, bw, bh)) bm |= 1u << w;
         }
         pair_blk[p] = (uint8_t)bm;
     }

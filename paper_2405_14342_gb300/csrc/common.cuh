@@ -281,6 +281,15 @@ __device__ __forceinline__ unsigned warp_digit_peers(uint32_t d, uint32_t mask, 
     return peers;
 }
 
+// Copy the first n_views view parameter sets into shared memory (block-wide).
+__device__ __forceinline__ void load_views_smem(ViewParams* sv, const ViewParams* views, int n_views) {
+    const int words = n_views * (int)(sizeof(ViewParams) / 4);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(views);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(sv);
+    for (int t = threadIdx.x; t < words; t += blockDim.x) dst[t] = src[t];
+    __syncthreads();
+}
+
 // Binary search of the view owning global tile t (tile_base ascending).
 __device__ __forceinline__ int view_of_tile(const ViewParams* views, int n_views, long long t) {
     int lo = 0, hi = n_views - 1;

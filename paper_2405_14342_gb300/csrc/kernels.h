@@ -90,7 +90,7 @@ void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs 
 void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeader* hdr_n_records,
                 unsigned long long rec_cap, unsigned long long* pair_off, unsigned long long* tile_sums,
                 StateHeader* hdr, unsigned long long pair_cap, cudaStream_t s);
-void emit_pairs(const ViewParams* views, const uint32_t* sorted_rec, const Record* recs, const uint2* rects,
+void emit_pairs(const ViewParams* views, int n_views, const uint32_t* sorted_rec, const Record* recs, const uint2* rects,
                 const unsigned long long* pair_off, const StateHeader* hdr, unsigned long long rec_cap,
                 uint32_t* pair_keys, uint32_t* pair_vals, unsigned long long pair_cap, cudaStream_t s);
 // Tile ranges of the sorted pairs; each pair's record mean + conic copied into

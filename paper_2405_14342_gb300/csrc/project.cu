@@ -151,14 +151,6 @@ __device__ __forceinline__ bool project_surfel(const ViewParams& v, const Consts
     return true;
 }
 
-__device__ __forceinline__ void load_views_smem(ViewParams* sv, const ViewParams* views, int n_views) {
-    const int words = n_views * (int)(sizeof(ViewParams) / 4);
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(views);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(sv);
-    for (int t = threadIdx.x; t < words; t += blockDim.x) dst[t] = src[t];
-    __syncthreads();
-}
-
 constexpr int kProjThreads = 256;
 
 __global__ void __launch_bounds__(kProjThreads) cull_k(const ViewParams* __restrict__ views, int n_views, Consts k,
