@@ -200,14 +200,18 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         bool hit = false;
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
-        if (j < wmax) {
-            hit = (a.pair_blk[start + j] >> warp) & 1u && rogs_ok(start + j < k.pair_cap, 201u);
+        if (j < wmax && rogs_ok(start + j < k.pair_cap, 201u)) {
+            // records and mean/conic loaded with the block masks (one round trip)
+            const uint32_t bm = a.pair_blk[start + j];
+            const uint32_t r = a.pair_rec[start + j];
+            const float4 m0 = a.pair_mc[2ull * (start + j)], c0 = a.pair_mc[2ull * (start + j) + 1];
+            hit = (bm >> warp) & 1u;
             if (hit) {
-                rec = a.pair_rec[start + j];
+                rec = r;
                 hit = rogs_ok(rec < k.rec_cap, 202u);
                 if (hit) {
-                    m = a.pair_mc[2ull * (start + j)];
-                    c = a.pair_mc[2ull * (start + j) + 1];
+                    m = m0;
+                    c = c0;
                 }
             }
         }

@@ -94,6 +94,15 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
 
     // block masks of the next chunk are loaded one chunk ahead
     uint32_t bm_next = start + lane < end ? pair_blk[start + lane] : 0u;
+    // the first chunk's records and mean/conic are loaded with its block masks,
+    // whether or not the entry reaches the block (one round trip less)
+    uint32_t rec_first = 0;
+    float4 m_first = make_float4(0.f, 0.f, 0.f, 0.f), c_first = m_first;
+    if (start + lane < end && rogs_ok(start + lane < k.pair_cap, 101u)) {
+        rec_first = pair_rec[start + lane];
+        m_first = pair_mc[2ull * (start + lane)];
+        c_first = pair_mc[2ull * (start + lane) + 1];
+    }
     for (uint32_t base = start; base < end; base += 32) {
         if (__all_sync(kFull, done)) break;
         const uint32_t j = base + lane;
@@ -105,11 +114,12 @@ __global__ void __launch_bounds__(TW * TH, fwd_threads_per_sm<NCP>() / (TW * TH)
         if (j < end) {   // the block mask says whether the entry can reach this warp's block
             hit = (bm >> warp) & 1u && rogs_ok(j < k.pair_cap, 101u);
             if (hit) {
-                rec = pair_rec[j];
+                const bool first = base == start;
+                rec = first ? rec_first : pair_rec[j];
                 hit = rogs_ok(rec < k.rec_cap, 102u);
                 if (hit) {
-                    m = pair_mc[2ull * j];
-                    c = pair_mc[2ull * j + 1];
+                    m = first ? m_first : pair_mc[2ull * j];
+                    c = first ? c_first : pair_mc[2ull * j + 1];
                 }
             }
         }
