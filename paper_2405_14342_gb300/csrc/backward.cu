@@ -39,9 +39,22 @@ constexpr int kSubPad = 33;   // padded row stride of the per-warp tables
 static_assert(2 * kSubPad >= 6 + 3 + ROGS_MAX_CLASSES + 1, "a gradient row must fit the two table rows");
 constexpr int kBwdWarpsPerBlock = 2;
 
+// List entries per chunk, and the resident two-warp blocks per SM the kernel
+// is compiled for.  Up to 24 channels a chunk of 24 entries keeps a warp's
+// shared memory (10.3 KB) and registers (102) small enough for 10 blocks, 20
+// warps, per SM (16 with 32-entry chunks); dL/dout is reloaded from its
+// shared-memory row after phase B, so it is not live through it.  Measured:
+// 32-entry chunks at 16 warps 0.480 ms, 24 at 20 warps 0.478 ms, 16 at 24
+// warps 0.553 ms (twice the chunks).
+template <int NCP>
+__host__ __device__ constexpr int bwd_chunk() { return NCP <= 24 ? 24 : 32; }
+template <int NCP>
+__host__ __device__ constexpr int bwd_min_blocks() { return NCP <= 24 ? 10 : 1; }
+
 template <int NCP>
 __host__ __device__ constexpr int bwd_warp_floats() {
-    return 32 * 4 + 32 * 4 + 32 * NCP + 32 + 2 * 32 * kSubPad;
+    constexpr int KC = bwd_chunk<NCP>();
+    return KC * 4 + KC * 4 + 32 * NCP + KC + 2 * KC * kSubPad;   // s_m, s_c, s_f | s_G, s_rec, tables
 }
 
 // The loss gradient at one pixel for the fused training step (Eqs. 8, 9, 12),
@@ -107,12 +120,15 @@ __device__ __forceinline__ void red_add_v4(float* p, float x, float y, float z, 
 }
 
 template <int TW, int TH, int NCP, int GP>
-__global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArgs a) {
+__global__ void __launch_bounds__(32 * kBwdWarpsPerBlock, bwd_min_blocks<NCP>()) composite_bwd_k(BwdArgs a) {
     pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     constexpr int BW = block_w(TW, TH), BH = 32 / BW, WX = TW / BW;
     constexpr int NW = TW * TH / 32;
     constexpr int GROUPS = NW / kBwdWarpsPerBlock;
     constexpr int SP = kSubPad;
+    constexpr int KC = bwd_chunk<NCP>();
+    constexpr uint32_t KCu = (uint32_t)KC;
+    static_assert(bwd_warp_floats<NCP>() % 4 == 0, "16-byte aligned warp regions");
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const long long tile = a.tile_order[blockIdx.x / GROUPS];
@@ -120,11 +136,11 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     extern __shared__ float4 smem_bwd[];
     float* wbase = reinterpret_cast<float*>(smem_bwd) + wib * bwd_warp_floats<NCP>();
     float4* s_m = reinterpret_cast<float4*>(wbase);
-    float4* s_c = s_m + 32;
-    float* s_f = reinterpret_cast<float*>(s_c + 32);
+    float4* s_c = s_m + KC;
+    float* s_f = reinterpret_cast<float*>(s_c + KC);   // KC feature rows, or 32 dL/dout rows (s_G)
     uint32_t* s_rec = reinterpret_cast<uint32_t*>(s_f + 32 * NCP);
-    float* s_w = reinterpret_cast<float*>(s_rec + 32);
-    float* s_p = s_w + 32 * SP;
+    float* s_w = reinterpret_cast<float*>(s_rec + KC);
+    float* s_p = s_w + KC * SP;
     float* s_G = s_f;   // dL/dout rows per pixel, written over the features once phase A is done
 
     const Consts& k = a.k;
@@ -195,12 +211,12 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     // memory asynchronously while the loss gradient runs.
     unsigned mask_first = 0;
     {
-        const uint32_t cbeg = wmax > 32u ? wmax - 32u : 0u;
+        const uint32_t cbeg = wmax > KCu ? wmax - KCu : 0u;
         const uint32_t j = cbeg + lane;
         bool hit = false;
         uint32_t rec = 0;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
-        if (j < wmax && rogs_ok(start + j < k.pair_cap, 201u)) {
+        if (lane < KC && j < wmax && rogs_ok(start + j < k.pair_cap, 201u)) {
             // records and mean/conic loaded with the block masks (one round trip)
             const uint32_t bm = a.pair_blk[start + j];
             const uint32_t r = a.pair_rec[start + j];
@@ -247,12 +263,12 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     // block masks of the chunk after the current one are loaded one chunk ahead
     uint32_t bm_next = 0;
     {
-        const uint32_t cb = wmax > 32u ? wmax - 32u : 0u;   // the second chunk is [cb - 32, cb)
-        const uint32_t j = (cb > 32u ? cb - 32u : 0u) + lane;
-        if (j < cb) bm_next = a.pair_blk[start + j];
+        const uint32_t cb = wmax > KCu ? wmax - KCu : 0u;   // the second chunk is [cb - KC, cb)
+        const uint32_t j = (cb > KCu ? cb - KCu : 0u) + lane;
+        if (lane < KC && j < cb) bm_next = a.pair_blk[start + j];
     }
     for (uint32_t cend = wmax; cend > 0;) {
-        const uint32_t cbeg = cend > 32u ? cend - 32u : 0u;
+        const uint32_t cbeg = cend > KCu ? cend - KCu : 0u;
         unsigned mask;
         if (cend == wmax) {
             mask = mask_first;   // staged before the loss gradient
@@ -260,13 +276,13 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
             const uint32_t j = cbeg + lane;   // index in the tile list
             const uint32_t bm = bm_next;
             {
-                const uint32_t jn = (cbeg > 32u ? cbeg - 32u : 0u) + lane;
-                bm_next = jn < cbeg ? a.pair_blk[start + jn] : 0u;
+                const uint32_t jn = (cbeg > KCu ? cbeg - KCu : 0u) + lane;
+                bm_next = lane < KC && jn < cbeg ? a.pair_blk[start + jn] : 0u;
             }
             bool hit = false;
             uint32_t rec = 0;
             float4 m = make_float4(0.f, 0.f, 0.f, 0.f), c = m;
-            if (j < cend) {   // the block mask says whether the entry can reach this warp's block
+            if (lane < KC && j < cend) {   // the block mask says whether the entry can reach this warp's block
                 hit = (bm >> warp) & 1u && rogs_ok(start + j < k.pair_cap, 203u);
                 if (hit) {
                     rec = a.pair_rec[start + j];
@@ -436,6 +452,11 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
         }
         const unsigned anym = __ballot_sync(kFull, any);
         __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NCP / 4; ++q) {   // dL/dout back from its row: not live through phase B
+            const float4 g4 = reinterpret_cast<const float4*>(s_G + lane * NCP)[q];
+            G[4 * q] = g4.x; G[4 * q + 1] = g4.y; G[4 * q + 2] = g4.z; G[4 * q + 3] = g4.w;
+        }
         // flush: each gradient row that received anything is added into the
         // record's row with 16-byte vector reductions, GP/4 lanes per row and
         // 128/GP rows per instruction (columns past 6 + nch add zeros)
@@ -485,9 +506,9 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock) composite_bwd_k(BwdArg
     }
 }
 
-static size_t bwd_smem_bytes(int ncp) {
-    return (size_t)kBwdWarpsPerBlock * 4 *
-           (size_t)(32 * 4 + 32 * 4 + 32 * ncp + 32 + 2 * 32 * kSubPad);
+template <int NCP>
+static size_t bwd_smem_bytes() {
+    return (size_t)kBwdWarpsPerBlock * 4 * (size_t)bwd_warp_floats<NCP>();
 }
 
 int bwd_loss_partials(long long total_tiles, int tile_w, int tile_h) {
@@ -501,7 +522,7 @@ static void bwd_attr() {
     cudaGetDevice(&dev);
     if (dev < 64 && !((done_mask >> dev) & 1ull)) {
         cudaFuncSetAttribute(composite_bwd_k<TW, TH, NCP, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)bwd_smem_bytes(NCP));
+                             (int)bwd_smem_bytes<NCP>());
         done_mask |= 1ull << dev;
     }
 }
@@ -525,7 +546,7 @@ static void launch_bwd_tile(int ncp, long long total_tiles, const BwdArgs& a, cu
 #define ROGS_BWD(NCP, GP)                                                                           \
     do {                                                                                            \
         bwd_attr<TW, TH, NCP, GP>();                                                                \
-        launch_pdl(composite_bwd_k<TW, TH, NCP, GP>, dim3(grid), dim3(32 * kBwdWarpsPerBlock), bwd_smem_bytes(NCP), s, a); \
+        launch_pdl(composite_bwd_k<TW, TH, NCP, GP>, dim3(grid), dim3(32 * kBwdWarpsPerBlock), bwd_smem_bytes<NCP>(), s, a); \
         note_launches(1);                                                                           \
     } while (0)
     switch (ncp) {
