@@ -41,7 +41,7 @@ LAMBDA_SMOOTH = 0.003             # Sec. 4.2 loss weight of the elevation smooth
 NCU_TRAFFIC = {
     # ncu --set full, one launch of the scene workload (6 x 960x540) at 16x16 tiles; see profiles/
     "composite_bwd": {"sha": "99dba5deb5586c16", "16x16": 295_786_752 + 54_563_584},
-    "composite_fwd": {"sha": "f52af6654668933b", "16x16": 75_639_296 + 259_831_040},
+    "composite_fwd": {"sha": "d2d036dc11587910", "16x16": 75_750_144 + 255_378_688},
 }
 
 
