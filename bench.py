@@ -366,25 +366,41 @@ def run_ours(args):
         host_loss = torch.empty(1, pin_memory=True)
         h2d = sum(int(x.numel() * x.element_size()) for x in pinned[0])
 
-        # The next step's targets are copied on a second stream while this step
-        # computes (double buffering over the n_h graphs' target buffers).
-        copy_stream = torch.cuda.Stream()
-        copied = [torch.cuda.Event() for _ in range(n_h)]
+        # The next step's targets are copied while this step computes (double
+        # buffering over the n_h graphs' target buffers), in 4 MB pieces spread
+        # over several copy streams so that several copy engines share the work.
+        n_cs = 4
+        copy_streams = [torch.cuda.Stream() for _ in range(n_cs)]
+        copied = [[torch.cuda.Event() for _ in range(n_cs)] for _ in range(n_h)]
         computed = [torch.cuda.Event() for _ in range(n_h)]
         for e in computed:
             e.record(stream)
+        piece = 4 << 20
+
+        def pieces(j):
+            out = []
+            for d, h in zip(targets[j], pinned[j]):
+                df, hf = d.view(-1), h.view(-1)
+                step_el = max(1, piece // d.element_size())
+                for a in range(0, df.numel(), step_el):
+                    out.append((df[a:a + step_el], hf[a:a + step_el]))
+            return out
+
+        plan = [pieces(j) for j in range(n_h)]
 
         def prefetch(k):
             j = k % n_h
-            copy_stream.wait_event(computed[j])          # the graph that last read buffer j is done
-            with torch.cuda.stream(copy_stream):
-                for d, h in zip(targets[j], pinned[j]):
-                    d.copy_(h, non_blocking=True)
-            copied[j].record(copy_stream)
+            for c, cs in enumerate(copy_streams):
+                cs.wait_event(computed[j])          # the graph that last read buffer j is done
+                with torch.cuda.stream(cs):
+                    for d, h in plan[j][c::n_cs]:
+                        d.copy_(h, non_blocking=True)
+                copied[j][c].record(cs)
 
         def step_host(k):
             j = k % n_h
-            stream.wait_event(copied[j])
+            for e in copied[j]:
+                stream.wait_event(e)
             graphs[j].launch()
             computed[j].record(stream)
             host_loss.copy_(loss, non_blocking=True)
