@@ -63,7 +63,7 @@ typedef struct {
     float box_half_x;           /* perspective box cull: |lateral| <= box_half_x (m) */
     float box_depth;            /* and 0 <= forward <= box_depth (m) */
     float jac_clamp;            /* EWA Jacobian evaluated at x/z clamped to +-jac_clamp*W/(2 fx) */
-    int32_t sort_tile;          /* radix sort keys per CTA: 2048, 4096 (default) or 8192 */
+    int32_t sort_tile;          /* pair sort keys per CTA: 1024, 2048, 4096 (default) or 8192 */
     int64_t record_capacity;    /* visible (view, surfel) records per render call */
     int64_t pair_capacity;      /* (tile, record) pairs per render call (<= 2^32-1) */
 } rogs_config;
@@ -244,6 +244,17 @@ rogs_status rogs_loss(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, c
                       const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
                       float lambda_s, float* loss, float* grad_out, rogs_stream stream);
 
+/* The same loss with the targets as 8-bit camera data, the form images and
+   segmentation maps are stored in (a third of the bytes of the FP32 / int32
+   form): tgt_rgb: device uint8 [3][pixels] planes per view, the colour target
+   cbar = value / 255 (rounded to the nearest float, so the loss equals
+   rogs_loss given those FP32 values bit for bit); label: device uint8
+   [pixels], a class id (a value >= C, 255 say, drops that pixel's semantic
+   term); mask as in rogs_loss. */
+rogs_status rogs_loss_u8(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, const float* out,
+                         const uint8_t* tgt_rgb, const uint8_t* label, const uint8_t* mask, float lambda_c,
+                         float lambda_s, float* loss, float* grad_out, rogs_stream stream);
+
 /* Backward of rogs_render_fwd (the adjoint of Eqs. 2, 5, 6, 7): reverse
    traversal of each tile's list from each pixel's last composited entry,
    recovering T by division, then the chain through the EWA projection.
@@ -271,6 +282,15 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
                             const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
                             float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
                             rogs_stream stream);
+
+/* rogs_train_step with 8-bit targets (tgt_rgb, label as in rogs_loss_u8):
+   the same results as rogs_train_step given cbar = value / 255 as FP32 and
+   the labels as int32, with 5 bytes of supervision per pixel instead of 17. */
+rogs_status rogs_train_step_u8(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                               const float* exposure_ab, int32_t n_exposure, float* out, void* state,
+                               const uint8_t* tgt_rgb, const uint8_t* label, const uint8_t* mask, float lambda_c,
+                               float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
+                               rogs_stream stream);
 
 /* Elevation smoothness loss (Sec. 3.3.2, smoothness equation, K = 4;
    neighbours as in the supplementary "Smooth Loss K Nearest Neighbor
@@ -465,6 +485,13 @@ rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, 
                                     void* state, const float* tgt_rgb, const int32_t* label, const uint8_t* mask,
                                     float lambda_c, float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
                                     rogs_stream stream, rogs_graph** graph);
+
+/* Same, capturing rogs_train_step_u8 (8-bit targets). */
+rogs_status rogs_train_graph_create_u8(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
+                                       int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
+                                       void* state, const uint8_t* tgt_rgb, const uint8_t* label, const uint8_t* mask,
+                                       float lambda_c, float lambda_s, float lambda_smooth, float* loss,
+                                       const rogs_grads* grads, rogs_stream stream, rogs_graph** graph);
 
 /* Same, forward only (rogs_render_fwd). */
 rogs_status rogs_render_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,

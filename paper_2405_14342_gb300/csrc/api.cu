@@ -285,8 +285,8 @@ bool valid_config(const rogs_config& c, std::string& err) {
     }
     if (!(c.t_min > 0.0f) || !(c.t_min < 1.0f)) { err = "need 0 < t_min < 1"; return false; }
     if (!(c.eps_dilate >= 0.0f)) { err = "eps_dilate must be >= 0"; return false; }
-    if (c.sort_tile != 2048 && c.sort_tile != 4096 && c.sort_tile != 8192) {
-        err = "sort_tile must be 2048, 4096 or 8192";
+    if (c.sort_tile != 1024 && c.sort_tile != 2048 && c.sort_tile != 4096 && c.sort_tile != 8192) {
+        err = "sort_tile must be 1024, 2048, 4096 or 8192";
         return false;
     }
     return true;
@@ -577,10 +577,12 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
         project_records(views, n_views, k, sp, ctx->bits, ctx->word_off, n_words, recs, rects,
                         (float*)(sb + L.rec_feat), ctx->dk_a, ctx->dv_a,
                         rcap, s);
-        // depth sort: stable on the binary32 depth key; ties keep (view, surfel) order
+        // depth sort: stable on the binary32 depth key; ties keep (view, surfel) order.
+        // The records are a few times fewer than the pairs: 1024 keys per CTA
+        // give its four passes enough CTAs to fill the SMs at every sort_tile.
         prof_mark(ctx, 1, s);
         radix_sort_pairs(ctx->dk_a, ctx->dv_a, ctx->dk_b, ctx->dv_b, ctx->dk_c, ctx->dv_c, &hdr->n_records, rcap, 32,
-                         ctx->hist, s, cfg.sort_tile);
+                         ctx->hist, s, kRsMinTile);
         prof_mark(ctx, 2, s);
         scan_pairs(ctx->dv_b, rects, hdr, rcap, ctx->pair_off, ctx->pair_tiles, hdr, pcap, s);
         emit_pairs(views, n_views, ctx->dv_b, recs, rects, ctx->pair_off, hdr, rcap, ctx->pk_a, ctx->pv_a, pcap, s);
@@ -606,12 +608,22 @@ rogs_status rogs_render_fwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     return ROGS_OK;
 }
 
-rogs_status rogs_loss(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, const float* out, const float* tgt_rgb,
-                      const int32_t* label, const uint8_t* mask, float lambda_c, float lambda_s, float* loss,
-                      float* grad_out, rogs_stream stream) {
+}  // extern "C"
+
+namespace {
+
+// The targets of one call are complete: colour planes, mask, and the labels
+// when the model has classes.
+bool targets_complete(const Targets& tg, int C) {
+    if (tg.rgb8) return tg.mask && (C == 0 || tg.label8);
+    return tg.rgb && tg.mask && (C == 0 || tg.label);
+}
+
+rogs_status loss_impl(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, const float* out, const Targets& tg,
+                      float lambda_c, float lambda_s, float* loss, float* grad_out, rogs_stream stream) {
     if (!ctx) return ROGS_ERR_INVALID;
     if (!cams || n_views < 1 || n_views > kMaxViews) return fail(ctx, ROGS_ERR_INVALID, "n_views out of range");
-    if (!out || !tgt_rgb || !mask || !loss || !grad_out || (ctx->cfg.num_classes > 0 && !label))
+    if (!out || !targets_complete(tg, ctx->cfg.num_classes) || !loss || !grad_out)
         return fail(ctx, ROGS_ERR_INVALID, "null device pointer");
     static thread_local ViewsArg va;
     long long tt, tp;
@@ -622,11 +634,30 @@ rogs_status rogs_loss(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, c
     if (st != ROGS_OK) return st;
     prof_mark(ctx, 5, s);
     upload_views(va, n_views, ctx->loss_views, nullptr, s);
-    loss_fwd_bwd(ctx->loss_views, n_views, tp, ctx->cfg.num_classes, out, tgt_rgb, label, mask, lambda_c, lambda_s,
+    loss_fwd_bwd(ctx->loss_views, n_views, tp, ctx->cfg.num_classes, out, tg, lambda_c, lambda_s,
                  loss, grad_out, ctx->loss_counter, ctx->loss_partials, (int)ctx->loss_cap, s);
     prof_mark(ctx, -1, s);
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rogs_status rogs_loss(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, const float* out, const float* tgt_rgb,
+                      const int32_t* label, const uint8_t* mask, float lambda_c, float lambda_s, float* loss,
+                      float* grad_out, rogs_stream stream) {
+    const Targets tg{tgt_rgb, label, nullptr, nullptr, mask};
+    return loss_impl(ctx, cams, n_views, out, tg, lambda_c, lambda_s, loss, grad_out, stream);
+}
+
+rogs_status rogs_loss_u8(rogs_ctx* ctx, const rogs_camera* cams, int32_t n_views, const float* out,
+                         const uint8_t* tgt_rgb, const uint8_t* label, const uint8_t* mask, float lambda_c,
+                         float lambda_s, float* loss, float* grad_out, rogs_stream stream) {
+    const Targets tg{nullptr, nullptr, tgt_rgb, label, mask};
+    if (!tgt_rgb) return ctx ? fail(ctx, ROGS_ERR_INVALID, "null device pointer") : ROGS_ERR_INVALID;
+    return loss_impl(ctx, cams, n_views, out, tg, lambda_c, lambda_s, loss, grad_out, stream);
 }
 
 rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
@@ -683,14 +714,17 @@ rogs_status rogs_render_bwd(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     return ROGS_OK;
 }
 
-rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
-                            const float* exposure_ab, int32_t n_exposure, float* out, void* state,
-                            const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
-                            float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
+}  // extern "C"
+
+namespace {
+
+rogs_status train_step_impl(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                            const float* exposure_ab, int32_t n_exposure, float* out, void* state, const Targets& tg,
+                            float lambda_c, float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
                             rogs_stream stream) {
     if (!ctx) return ROGS_ERR_INVALID;
     const rogs_config& cfg = ctx->cfg;
-    if (!tgt_rgb || !mask || !loss || !grads || (cfg.num_classes > 0 && !label))
+    if (!targets_complete(tg, cfg.num_classes) || !loss || !grads)
         return fail(ctx, ROGS_ERR_INVALID, "null target/loss/grads pointer");
     if (lambda_smooth != 0.0f && (!surfels || !surfels->grid_index || surfels->grid_w <= 0 || surfels->grid_h <= 0))
         return fail(ctx, ROGS_ERR_INVALID, "smoothness loss needs the grid index map");
@@ -711,7 +745,7 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     // backward waits for them
     ROGS_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
     ROGS_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-    mask_count(mask, total_pix, ctx->loss_counter, ctx->side);
+    mask_count(tg.mask, total_pix, ctx->loss_counter, ctx->side);
     if (lambda_smooth != 0.0f)
         smooth_loss(surfels->grid_index, surfels->grid_w, surfels->grid_h, surfels->xyz, lambda_smooth,
                     ctx->smooth_val, grads->xyz, ctx->smooth_partials, ctx->side);
@@ -740,7 +774,7 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     a.pix_T = (const float*)(sb + L.pix_T);
     a.pix_last = (const uint32_t*)(sb + L.pix_last);
     a.grad_out = nullptr;
-    a.out = out; a.tgt_rgb = tgt_rgb; a.label = label; a.mask = mask; a.mask_count = ctx->loss_counter;
+    a.out = out; a.tg = tg; a.mask_count = ctx->loss_counter;
     a.lambda_c = lambda_c; a.lambda_s = lambda_s; a.loss_partials = ctx->loss_partials;
     a.rec_grad = ctx->rec_grad; a.d_exposure = grads->exposure;
     prof_mark(ctx, 6, s);
@@ -758,6 +792,31 @@ rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const ro
     ROGS_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join2, 0));
     ROGS_CUDA(ctx, cudaGetLastError());
     return ROGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rogs_status rogs_train_step(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                            const float* exposure_ab, int32_t n_exposure, float* out, void* state,
+                            const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c,
+                            float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
+                            rogs_stream stream) {
+    const Targets tg{tgt_rgb, label, nullptr, nullptr, mask};
+    return train_step_impl(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, tg, lambda_c, lambda_s,
+                           lambda_smooth, loss, grads, stream);
+}
+
+rogs_status rogs_train_step_u8(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams, int32_t n_views,
+                               const float* exposure_ab, int32_t n_exposure, float* out, void* state,
+                               const uint8_t* tgt_rgb, const uint8_t* label, const uint8_t* mask, float lambda_c,
+                               float lambda_s, float lambda_smooth, float* loss, const rogs_grads* grads,
+                               rogs_stream stream) {
+    if (!tgt_rgb) return ctx ? fail(ctx, ROGS_ERR_INVALID, "null target/loss/grads pointer") : ROGS_ERR_INVALID;
+    const Targets tg{nullptr, nullptr, tgt_rgb, label, mask};
+    return train_step_impl(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, tg, lambda_c, lambda_s,
+                           lambda_smooth, loss, grads, stream);
 }
 
 rogs_status rogs_smooth_loss(rogs_ctx* ctx, const rogs_surfels* surfels, float lambda_smooth, float* loss,
@@ -981,6 +1040,21 @@ rogs_status rogs_train_graph_create(rogs_ctx* ctx, const rogs_surfels* surfels, 
     if (st != ROGS_OK) return st;
     st = rogs_train_step(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, tgt_rgb, label, mask,
                          lambda_c, lambda_s, lambda_smooth, loss, grads, stream);
+    return finish_capture(ctx, s, st, gout);
+}
+
+rogs_status rogs_train_graph_create_u8(rogs_ctx* ctx, const rogs_surfels* surfels, const rogs_camera* cams,
+                                       int32_t n_views, const float* exposure_ab, int32_t n_exposure, float* out,
+                                       void* state, const uint8_t* tgt_rgb, const uint8_t* label, const uint8_t* mask,
+                                       float lambda_c, float lambda_s, float lambda_smooth, float* loss,
+                                       const rogs_grads* grads, rogs_stream stream, rogs_graph** gout) {
+    if (!ctx || !gout) return ROGS_ERR_INVALID;
+    *gout = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    rogs_status st = begin_capture(ctx, surfels, cams, n_views, s, true);
+    if (st != ROGS_OK) return st;
+    st = rogs_train_step_u8(ctx, surfels, cams, n_views, exposure_ab, n_exposure, out, state, tgt_rgb, label, mask,
+                            lambda_c, lambda_s, lambda_smooth, loss, grads, stream);
     return finish_capture(ctx, s, st, gout);
 }
 

@@ -167,8 +167,9 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock, bwd_min_blocks<NCP>())
     // with the fused loss its pixels only count if they are in the mask, so a
     // warp there reads the mask first and, if none of its pixels is in it,
     // leaves a zero loss partial without loading anything else.
-    if (a.tgt_rgb && trange.y <= trange.x) {
-        const bool m = inside && a.mask[v.pix_base + (long long)py * W + px] != 0;
+    const bool fused = a.tg.rgb != nullptr || a.tg.rgb8 != nullptr;
+    if (fused && trange.y <= trange.x) {
+        const bool m = inside && a.tg.mask[v.pix_base + (long long)py * W + px] != 0;
         if (!__any_sync(kFull, m)) {
             if (a.loss_partials && lane == 0) a.loss_partials[blockIdx.x * kBwdWarpsPerBlock + wib] = 0.0f;
             return;
@@ -177,7 +178,6 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock, bwd_min_blocks<NCP>())
     // Every input of this lane's pixel is loaded at once, one memory round trip:
     // the forward's transmittance and last contributor, and either dL/dout or
     // (fused loss) the output channels, the targets and the mask
-    const bool fused = a.tgt_rgb != nullptr;
     float T = 1.0f;
     uint32_t last = 0;
     float G[NCP];
@@ -194,10 +194,8 @@ __global__ void __launch_bounds__(32 * kBwdWarpsPerBlock, bwd_min_blocks<NCP>())
 #pragma unroll
         for (int ch = 0; ch < NCP; ++ch) G[ch] = ch < nch ? src[ch * plane] : 0.0f;
         if (fused) {
-            const float* t = a.tgt_rgb + 3ll * v.pix_base + q;
-            t0 = t[0]; t1 = t[plane]; t2 = t[2 * plane];
-            in_mask = a.mask[pix] != 0;
-            lb = C > 0 ? a.label[pix] : -1;
+            load_pixel_target(a.tg, 3ll * v.pix_base + q, plane, pix, C, t0, t1, t2, lb);
+            in_mask = a.tg.mask[pix] != 0;
         }
     } else {
 #pragma unroll

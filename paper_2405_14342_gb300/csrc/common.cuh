@@ -230,6 +230,53 @@ __device__ __forceinline__ float surfel_alpha(float dx, float dy, float A2, floa
     return fminf(alpha_max, __fmul_rn(alpha, g));
 }
 
+// Supervision of the loss (Eqs. 8, 9), in the output's pixel order: colour
+// planes [3][pixels] per view and one class label per pixel, either as FP32
+// and int32 or as 8-bit camera data (colour = value / 255, label = class id);
+// exactly one of rgb / rgb8 is set.  A label outside [0, C) drops the pixel's
+// semantic term.
+struct Targets {
+    const float* rgb;
+    const int32_t* label;
+    const uint8_t* rgb8;
+    const uint8_t* label8;
+    const uint8_t* mask;   // 1 = the pixel is in M
+};
+
+// x / 255 rounded to the nearest float, for an integer x in [0, 255]: an
+// 8-bit colour value as a fraction of full scale.  The product with the
+// rounded reciprocal is corrected once by its residual x - 255 q, which one FMA
+// gives exactly (Markstein's correction step); q + residual / 255 then rounds
+// to the same float as the IEEE quotient for all 256 inputs (the plain product
+// misses it for 126 of them).
+__device__ __forceinline__ float unit_from_u8(uint32_t x) {
+    const float xf = (float)x;
+    constexpr float r = 1.0f / 255.0f;
+    const float q = __fmul_rn(xf, r);
+    const float e = __fmaf_rn(-q, 255.0f, xf);
+    return __fmaf_rn(e, r, q);
+}
+
+// One pixel's supervision (Eqs. 8, 9) from either target format: the three
+// colour values (colour planes start at rgb_base, `plane` pixels apart) and
+// the class label (-1 when C = 0).
+__device__ __forceinline__ void load_pixel_target(const Targets& tg, long long rgb_base, long long plane,
+                                                  long long pix, int C, float& t0, float& t1, float& t2, int& lb) {
+    if (tg.rgb8) {
+        const uint8_t* t = tg.rgb8 + rgb_base;
+        t0 = unit_from_u8(t[0]);
+        t1 = unit_from_u8(t[plane]);
+        t2 = unit_from_u8(t[2 * plane]);
+        lb = C > 0 ? (int)tg.label8[pix] : -1;
+    } else {
+        const float* t = tg.rgb + rgb_base;
+        t0 = t[0];
+        t1 = t[plane];
+        t2 = t[2 * plane];
+        lb = C > 0 ? tg.label[pix] : -1;
+    }
+}
+
 // Conservative test: can the entry reach a >= alpha_min at some pixel centre
 // of the bw x bh block whose first pixel is (bx, by)?  Uses the bounding box of
 // the ellipse d^T Q d <= 2 ln(alpha / alpha_min) (Q = conic), padded so that

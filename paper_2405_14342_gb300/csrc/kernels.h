@@ -62,7 +62,11 @@ struct GradPtrs {
 };
 
 // ---- sort.cu
-size_t radix_hist_words(unsigned long long cap);
+constexpr int kRsMinTile = 1024;   // smallest keys-per-CTA option of the radix sort (sizes the histograms)
+// Words of the digit histograms for up to `cap` keys: [256][tiles] counts, then the 256 digit totals.
+constexpr size_t radix_hist_words(unsigned long long cap) {
+    return (size_t)(256ull * (cap == 0 ? 1ull : (cap + kRsMinTile - 1) / kRsMinTile) + 256ull);
+}
 void prepare_sort();   // set the dynamic shared-memory limits (before any capture)
 void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout, uint32_t* kalt,
                       uint32_t* valt, const unsigned long long* n_ptr, unsigned long long cap, int key_bits,
@@ -135,9 +139,7 @@ struct BwdArgs {
     // dL/dout: either grad_out, or (fused training step) computed from these
     const float* grad_out;
     const float* out;
-    const float* tgt_rgb;
-    const int32_t* label;
-    const uint8_t* mask;
+    Targets tg;   // fused: tg.rgb or tg.rgb8 set
     const unsigned long long* mask_count;
     float lambda_c, lambda_s;
     float* loss_partials;   // one per warp of the launch, or null
@@ -185,7 +187,7 @@ void smooth_loss(const int32_t* grid_index, int grid_w, int grid_h, const float*
 
 // ---- loss.cu
 void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, int C, const float* out,
-                  const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c, float lambda_s,
+                  const Targets& tg, float lambda_c, float lambda_s,
                   float* loss, float* grad_out, unsigned long long* counter, float* partials, int n_blocks_cap,
                   cudaStream_t s);
 int loss_blocks(long long total_pixels);

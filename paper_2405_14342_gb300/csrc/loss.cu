@@ -45,9 +45,7 @@ __global__ void __launch_bounds__(kLossThreads) mask_count_k(const uint8_t* __re
 
 __global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restrict__ views, int n_views,
                                                        long long total_pixels, int C, const float* __restrict__ out,
-                                                       const float* __restrict__ tgt_rgb,
-                                                       const int32_t* __restrict__ label,
-                                                       const uint8_t* __restrict__ mask, float lambda_c,
+                                                       const Targets tg, float lambda_c,
                                                        float lambda_s, const unsigned long long* __restrict__ counter,
                                                        float* __restrict__ grad_out, float* __restrict__ partials) {
     pdl_wait();   // after the previous kernel of the stream (programmatic launch)
@@ -63,20 +61,21 @@ __global__ void __launch_bounds__(kLossThreads) loss_k(const ViewParams* __restr
         const float* o = out + (long long)nch * v.pix_base + q;
         float* g = grad_out + (long long)nch * v.pix_base + q;
         const unsigned long long nm = *counter;
-        const bool m = mask[p] != 0 && nm > 0;
+        const bool m = tg.mask[p] != 0 && nm > 0;
         if (!m) {
             for (int ch = 0; ch < nch; ++ch) g[ch * plane] = 0.0f;
         } else {
             const float inv = 1.0f / (float)nm;
-            const float* t = tgt_rgb + 3ll * v.pix_base + q;
+            float tr[3];
+            int lb;
+            load_pixel_target(tg, 3ll * v.pix_base + q, plane, p, C, tr[0], tr[1], tr[2], lb);
             float l1 = 0.0f;
             for (int ch = 0; ch < 3; ++ch) {
-                const float d = o[ch * plane] - t[ch * plane];
+                const float d = o[ch * plane] - tr[ch];
                 l1 += fabsf(d);
                 g[ch * plane] = lambda_c * inv * (d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f));
             }
             float ce = 0.0f;
-            const int lb = C > 0 ? label[p] : -1;
             if (lb >= 0 && lb < C) {  // labels outside [0, C) carry no semantic term
                 // softmax with one exponential per class: e = exp(x - max), p = e / sum e
                 float mx = o[3 * plane];
@@ -149,16 +148,16 @@ __global__ void __launch_bounds__(1024) loss_final_k(const float* __restrict__ p
 }
 
 void loss_fwd_bwd(const ViewParams* views, int n_views, long long total_pixels, int C, const float* out,
-                  const float* tgt_rgb, const int32_t* label, const uint8_t* mask, float lambda_c, float lambda_s,
+                  const Targets& tg, float lambda_c, float lambda_s,
                   float* loss, float* grad_out, unsigned long long* counter, float* partials, int n_blocks_cap,
                   cudaStream_t s) {
     const int nb = loss_blocks(total_pixels);
     cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     int gc = nb < 152 * 8 ? nb : 152 * 8;
     if (gc < 1) gc = 1;
-    launch_pdl(mask_count_k, dim3(gc), dim3(kLossThreads), 0, s, mask, total_pixels, counter);
-    launch_pdl(loss_k, dim3(nb > 0 ? nb : 1), dim3(kLossThreads), 0, s, views, n_views, total_pixels, C, out, tgt_rgb, label, mask,
-                                                    lambda_c, lambda_s, counter, grad_out, partials);
+    launch_pdl(mask_count_k, dim3(gc), dim3(kLossThreads), 0, s, tg.mask, total_pixels, counter);
+    launch_pdl(loss_k, dim3(nb > 0 ? nb : 1), dim3(kLossThreads), 0, s, views, n_views, total_pixels, C, out, tg,
+               lambda_c, lambda_s, counter, grad_out, partials);
     launch_pdl(loss_final_k, dim3(1), dim3(1024), 0, s, partials, nb, counter, nullptr, loss);
     note_launches(3);
     (void)n_blocks_cap;

@@ -24,12 +24,11 @@
 namespace rogs {
 
 constexpr unsigned long long kNoallocMaxPairs = ROGS_NOALLOC_MAX_PAIRS;
-// histogram words as the sort lays them out (sized for its smallest keys-per-CTA, 2048)
-constexpr unsigned long long kNoallocTiles = (kNoallocMaxPairs + 2047ull) / 2048ull;
-constexpr unsigned long long kNoallocHistWords = 256ull * kNoallocTiles + 256ull;     // histograms + digit totals
+// histogram words as the sort lays them out (sized for its smallest keys-per-CTA)
+constexpr unsigned long long kNoallocHistWords = radix_hist_words(kNoallocMaxPairs);   // histograms + digit totals
 constexpr unsigned long long kNoallocWords = 2ull * kNoallocMaxPairs + kNoallocHistWords;
 
-// alternate keys | alternate values | digit histograms (8.91 MB for 2^20 pairs)
+// alternate keys | alternate values | digit histograms (9.44 MB for 2^20 pairs)
 static __device__ __align__(256) uint32_t g_sort_scratch[kNoallocWords];
 
 namespace {
@@ -67,7 +66,6 @@ extern "C" rogs_status rogs_sort_pairs_noalloc(const uint32_t* keys_in, const ui
     uint32_t* kalt = base;
     uint32_t* valt = base + kNoallocMaxPairs;
     uint32_t* hist = base + 2 * kNoallocMaxPairs;
-    static_assert(kNoallocHistWords >= 256ull * ((kNoallocMaxPairs + 2047ull) / 2048ull) + 256ull, "histogram room");
     radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, kalt, valt, nullptr, (unsigned long long)n, key_bits, hist,
                      (cudaStream_t)stream, 4096);
     if (clean_on_entry && cudaPeekAtLastError() != cudaSuccess) {

@@ -1,14 +1,15 @@
 // sort.cu -- hand-written stable LSD radix sort of (uint32 key, uint32 value)
-// pairs with a device-resident length (8-bit digits, 2048-8192 keys per CTA).
+// pairs with a device-resident length (8-bit digits, 1024-8192 keys per CTA).
 //
-// Keys per CTA (the sort "chunk") is 2048, 4096 or 8192 (8/16/32 keys per
-// thread), chosen by the context configuration.  Per pass, three launches
+// Keys per CTA (the sort "chunk") is 1024, 2048, 4096 or 8192 (4/8/16/32
+// keys per thread), chosen by the caller: the context configuration for the
+// pair sort, 1024 for the depth sort of the records.  Per pass, three launches
 // with fixed grids:
 //   rs_upsweep_k   per-tile digit histograms, digit-major [256][tiles]
 //   rs_rowscan_k   one block per digit: exclusive scan across tiles + digit total
 //   rs_downsweep_k stable scatter: the rank of a key inside its tile is built
-//                  warp by warp in key order (__match_any_sync groups equal
-//                  digits, lanes below a lane come first), then warps in
+//                  warp by warp in key order (one ballot per digit bit
+//                  groups equal digits, lanes below a lane come first), then warps in
 //                  order, so equal keys keep their input order.
 // No block waits on another block.  Used for the depth sort of visible
 // records and the tile sort of (tile, record) pairs (RoGs Sec. 3.3.1: sort by
@@ -20,7 +21,6 @@ namespace rogs {
 
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsMinTile = 2048;   // smallest keys-per-CTA option (sizes the histograms)
 
 __device__ __forceinline__ unsigned long long rs_len(const unsigned long long* n_ptr, unsigned long long cap) {
     return scan_len(n_ptr, cap);
@@ -210,15 +210,10 @@ __global__ void copy_pairs_k(const uint32_t* kin, const uint32_t* vin, uint32_t*
 }
 
 void prepare_sort() {
+    cudaFuncSetAttribute(rs_downsweep_k<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_stage_bytes(4));
     cudaFuncSetAttribute(rs_downsweep_k<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_stage_bytes(8));
     cudaFuncSetAttribute(rs_downsweep_k<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_stage_bytes(16));
     cudaFuncSetAttribute(rs_downsweep_k<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_stage_bytes(32));
-}
-
-size_t radix_hist_words(unsigned long long cap) {
-    unsigned long long t = (cap + kRsMinTile - 1) / kRsMinTile;
-    if (t == 0) t = 1;
-    return (size_t)(256 * t + 256);
 }
 
 template <int IPT>
@@ -260,7 +255,9 @@ void radix_sort_pairs(const uint32_t* kin, const uint32_t* vin, uint32_t* kout, 
         note_launches(1);
         return;
     }
-    if (sort_tile == 2048)
+    if (sort_tile == 1024)
+        radix_passes<4>(kin, vin, kout, vout, kalt, valt, n_ptr, cap, key_bits, hist, row_total, s);
+    else if (sort_tile == 2048)
         radix_passes<8>(kin, vin, kout, vout, kalt, valt, n_ptr, cap, key_bits, hist, row_total, s);
     else if (sort_tile == 8192)
         radix_passes<32>(kin, vin, kout, vout, kalt, valt, n_ptr, cap, key_bits, hist, row_total, s);

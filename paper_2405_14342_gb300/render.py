@@ -149,6 +149,9 @@ class Renderer:
 
     def loss(self, frame: Frame, tgt_rgb, label, mask, lambda_c=1.0, lambda_s=0.06, loss=None, grad_out=None,
              stream=None):
+        """Masked L1 + CE loss and dL/dout (rogs_loss).  Targets in the output
+        pixel order: float32 colour planes with int32 labels, or uint8 colour
+        planes (value / 255) with uint8 labels (rogs_loss_u8); uint8 mask."""
         self._own(frame)
         if loss is None:
             loss = torch.empty(1, dtype=torch.float32, device=self.device)
@@ -178,7 +181,8 @@ class Renderer:
                    loss: torch.Tensor, grads: dict, lambda_c=1.0, lambda_s=0.06, stream=None, lambda_smooth=0.0):
         """Forward, masked L1 + CE loss and backward with the loss fused into the
         backward kernel (rogs_train_step), plus lambda_smooth L_smooth when
-        nonzero; gradients are added into `grads`."""
+        nonzero; gradients are added into `grads`.  Targets as in loss():
+        uint8 colour and labels take rogs_train_step_u8."""
         self._own(frame)
         frame.generation += 1
         R.rogs_train_step(self.ctx, m.c_struct(), frame.cam_arr, len(frame.cams), exposure, frame.out, frame.state,

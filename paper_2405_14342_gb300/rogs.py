@@ -145,6 +145,8 @@ def lib():
                                       P, P, P, P, P, C.c_float, C.c_float, C.c_float, P, C.POINTER(rogs_grads), P]
         L.rogs_render_graph_create.argtypes = [P, C.POINTER(rogs_surfels), C.POINTER(rogs_camera), C.c_int32, P,
                                                C.c_int32, P, P, P, C.POINTER(P)]
+        for base in ("rogs_loss", "rogs_train_step", "rogs_train_graph_create"):   # 8-bit target forms
+            getattr(L, base + "_u8").argtypes = getattr(L, base).argtypes
         L.rogs_graph_launch.argtypes = [P, P]
         L.rogs_graph_destroy.argtypes = [P]
         L.rogs_graph_destroy.restype = None
@@ -171,7 +173,8 @@ def lib():
                      "rogs_serve_get_stats", "rogs_serve_set_timeout", "rogs_measure_fp32_peak", "rogs_train_graph_create", "rogs_render_graph_create", "rogs_graph_launch",
                      "rogs_profile_enable", "rogs_profile_read","rogs_default_config", "rogs_create", "rogs_reserve", "rogs_state_layout_of",
                      "rogs_state_counts", "rogs_init_from_poses", "rogs_render_fwd", "rogs_loss",
-                     "rogs_render_bwd", "rogs_sort_pairs"):
+                     "rogs_render_bwd", "rogs_sort_pairs", "rogs_loss_u8", "rogs_train_step_u8",
+                     "rogs_train_graph_create_u8"):
             getattr(L, name).restype = S
         _lib = L
     return _lib
@@ -185,6 +188,19 @@ def _check(ctx, st):
 
 def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _target_entry(name, tgt_rgb, label):
+    """The C entry for the targets' format: FP32 colour planes with int32
+    labels (`name`), or 8-bit colour planes and labels (`name`_u8)."""
+    import torch
+    if tgt_rgb.dtype == torch.uint8:
+        if label is not None and label.dtype != torch.uint8:
+            raise TypeError("8-bit colour targets take uint8 labels")
+        return getattr(lib(), name + "_u8")
+    if tgt_rgb.dtype != torch.float32 or (label is not None and label.dtype != torch.int32):
+        raise TypeError("targets are float32 colour with int32 labels, or uint8 colour with uint8 labels")
+    return getattr(lib(), name)
 
 
 def _stream(stream=None):
@@ -301,7 +317,7 @@ def rogs_render_fwd(ctx, surf: rogs_surfels, cam_arr, n_views, exposure_ab, out,
 
 
 def rogs_loss(ctx, cam_arr, n_views, out, tgt_rgb, label, mask, lambda_c, lambda_s, loss, grad_out, stream=None):
-    _check(ctx, lib().rogs_loss(ctx, cam_arr, n_views, _ptr(out), _ptr(tgt_rgb), _ptr(label), _ptr(mask),
+    _check(ctx, _target_entry("rogs_loss", tgt_rgb, label)(ctx, cam_arr, n_views, _ptr(out), _ptr(tgt_rgb), _ptr(label), _ptr(mask),
                                 float(lambda_c), float(lambda_s), _ptr(loss), _ptr(grad_out), _stream(stream)))
 
 
@@ -372,7 +388,7 @@ def rogs_launch_count() -> int:
 def rogs_train_graph_create(ctx, surf, cam_arr, n_views, exposure_ab, out, state, tgt_rgb, label, mask, lambda_c,
                             lambda_s, loss, grads: rogs_grads, stream=None, lambda_smooth=0.0):
     g = C.c_void_p()
-    _check(ctx, lib().rogs_train_graph_create(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
+    _check(ctx, _target_entry("rogs_train_graph_create", tgt_rgb, label)(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
                                               int(exposure_ab.shape[0]), _ptr(out), _ptr(state), _ptr(tgt_rgb),
                                               _ptr(label), _ptr(mask), float(lambda_c), float(lambda_s),
                                               float(lambda_smooth), _ptr(loss),
@@ -382,7 +398,7 @@ def rogs_train_graph_create(ctx, surf, cam_arr, n_views, exposure_ab, out, state
 
 def rogs_train_step(ctx, surf, cam_arr, n_views, exposure_ab, out, state, tgt_rgb, label, mask, lambda_c, lambda_s,
                     loss, grads: rogs_grads, stream=None, lambda_smooth=0.0):
-    _check(ctx, lib().rogs_train_step(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
+    _check(ctx, _target_entry("rogs_train_step", tgt_rgb, label)(ctx, C.byref(surf), cam_arr, n_views, _ptr(exposure_ab),
                                       int(exposure_ab.shape[0]), _ptr(out), _ptr(state), _ptr(tgt_rgb), _ptr(label),
                                       _ptr(mask), float(lambda_c), float(lambda_s), float(lambda_smooth), _ptr(loss),
                                       C.byref(grads),

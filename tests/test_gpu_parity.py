@@ -80,7 +80,7 @@ def compare_forward(R, rr, m, cams, ex, depth_scale, max_band_frac=1e-4, max_ban
 
 # ---------------------------------------------------------------- sort
 
-@pytest.mark.parametrize("sort_tile", [2048, 4096, 8192])
+@pytest.mark.parametrize("sort_tile", [1024, 2048, 4096, 8192])
 @pytest.mark.parametrize("n,bits", [(1, 32), (4095, 8), (4096, 18), (4097, 32), (123457, 18), (1 << 20, 32),
                                     (250001, 5), (1999999, 24)])
 def test_radix_sort_is_stable_and_exact(R, n, bits, sort_tile):

@@ -53,3 +53,42 @@ def test_tune_picks_the_fastest_candidate_and_caches_it(tmp_path, monkeypatch):
     other, _ = autotune.tune(_Map(), [cams], None, None, 8, 1, 1, cache_path=path)
     assert calls and other == {"tile": (16, 16), "sort_tile": 2048}
     assert len(json.load(open(path))) == 2
+
+
+def _round_binary32(x):
+    """Exact rational -> nearest binary32 (ties to even), as an exact rational."""
+    from fractions import Fraction
+    if x == 0:
+        return Fraction(0)
+    s, a = (-1 if x < 0 else 1), abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    ulp = Fraction(2) ** (e - 23)
+    m = a / ulp
+    n, rem = divmod(m.numerator, m.denominator)
+    if 2 * rem > m.denominator or (2 * rem == m.denominator and n % 2 == 1):
+        n += 1
+    return s * n * ulp
+
+
+def test_u8_colour_conversion_rounds_like_ieee_division():
+    """The kernels' 8-bit colour conversion (unit_from_u8: q = RN(x r) with
+    r = RN(1/255), one exact FMA residual x - 255 q, then RN(q + residual r),
+    Markstein's correction step) is the correctly rounded x / 255 for all 256
+    inputs, in exact arithmetic; the plain product RN(x r) is not."""
+    from fractions import Fraction
+    import numpy as np
+    r = _round_binary32(Fraction(1, 255))
+    wrong_plain = 0
+    for x in range(256):
+        q = _round_binary32(x * r)
+        e = x - 255 * q
+        assert _round_binary32(e) == e                        # the FMA residual is exact
+        ref = _round_binary32(Fraction(x, 255))
+        assert _round_binary32(q + e * r) == ref, x
+        assert float(ref) == float(np.float32(x) / np.float32(255))
+        wrong_plain += q != ref
+    assert wrong_plain > 0
