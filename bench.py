@@ -252,7 +252,10 @@ def run_ours(args):
                 "config": {"tile": f"{tile[0]}x{tile[1]}", "sort_tile": sort_tile, "timesteps_resident": n_t}}
 
     # ---- batched, graph-captured form (headline): one graph per timestep
-    graphs = [rr.train_graph(st, frames[k], exposure, *targets[k], loss, grads, lambda_smooth=LAMBDA_SMOOTH)
+    # one loss scalar per graph, so that a step's loss can be read back while
+    # the next step runs
+    losses = [torch.empty(1, device="cuda") for _ in range(n_t)]
+    graphs = [rr.train_graph(st, frames[k], exposure, *targets[k], losses[k], grads, lambda_smooth=LAMBDA_SMOOTH)
               for k in range(n_t)]
     for k in range(args.warmup):
         graphs[k % n_t].launch()
@@ -365,17 +368,22 @@ def run_ours(args):
     if not args.no_e2e:
         n_h = min(8, n_t)
         pinned = [tuple(x.cpu().pin_memory() for x in targets[k]) for k in range(n_h)]
-        host_loss = torch.empty(1, pin_memory=True)
+        host_loss = torch.empty(n_h, pin_memory=True)
         h2d = sum(int(x.numel() * x.element_size()) for x in pinned[0])
 
         # The next step's targets are copied while this step computes (double
         # buffering over the n_h graphs' target buffers), in 4 MB pieces spread
-        # over several copy streams so that several copy engines share the work.
+        # over several copy streams so that several copy engines share the work;
+        # each step's loss is read back on a stream of its own once the step is
+        # done, beside the next step (a copy on the compute stream would sit
+        # between two graphs: 8 us a step).
         n_cs = 4
         copy_streams = [torch.cuda.Stream() for _ in range(n_cs)]
+        d2h_stream = torch.cuda.Stream()
         copied = [[torch.cuda.Event() for _ in range(n_cs)] for _ in range(n_h)]
         computed = [torch.cuda.Event() for _ in range(n_h)]
-        for e in computed:
+        read = [torch.cuda.Event() for _ in range(n_h)]
+        for e in computed + read:
             e.record(stream)
         piece = 4 << 20
 
@@ -403,15 +411,24 @@ def run_ours(args):
             j = k % n_h
             for e in copied[j]:
                 stream.wait_event(e)
+            stream.wait_event(read[j])            # graph j's previous loss has been read
             graphs[j].launch()
             computed[j].record(stream)
-            host_loss.copy_(loss, non_blocking=True)
+            d2h_stream.wait_event(computed[j])
+            with torch.cuda.stream(d2h_stream):
+                host_loss[j:j + 1].copy_(losses[j], non_blocking=True)
+            read[j].record(d2h_stream)
             prefetch(k + 1)
 
         prefetch(0)
         for k in range(args.warmup):
             step_host(k)
-        ems = _timed(lambda k: step_host(args.warmup + k), args.steps, world, dist)
+        def step_timed(k):
+            step_host(args.warmup + k)
+            if k == args.steps - 1:   # the timed region ends after the last loss read
+                stream.wait_event(read[(args.warmup + k) % n_h])
+
+        ems = _timed(step_timed, args.steps, world, dist)
         torch.cuda.synchronize()
         e2e = {"value": round(world * args.steps * P / (ems * 1e-3) / 1e6, 3), "unit": "Mpix/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
