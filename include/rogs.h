@@ -460,7 +460,7 @@ rogs_status rogs_serve_poll(rogs_server* srv, uint64_t ticket, void* host_out, i
 rogs_status rogs_serve_get_stats(rogs_server* srv, rogs_serve_stats* out);
 
 /* Change the server's timeout_s (thread-safe; > 0).  Batches already in
-   flight are judged against the new value from the next check on. */
+   flight are checked against the new value from the next check on. */
 rogs_status rogs_serve_set_timeout(rogs_server* srv, double timeout_s);
 
 /* Stop the worker, wait (bounded by timeout_s) for batches in flight, free
