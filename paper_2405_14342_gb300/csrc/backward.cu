@@ -23,7 +23,8 @@
 // conic inverse, Sigma' = T2 T2^T + eps I, T2 = J W M, the perspective
 // Jacobian and mean, the quaternion normalisation and M = R[:, :2] diag(s),
 // and adds the per-surfel results (several views touch one surfel) with
-// atomics; then each warp walks its 32 records with lane = colour/semantic
+// atomics (one vector reduction for a quaternion row and one for a scale
+// row); then each warp walks its 32 records with lane = colour/semantic
 // column, so the feature gradients leave as coalesced atomics.  Every row is
 // cleared after it is read, so the buffer is all zero again for the next
 // backward.
@@ -41,7 +42,7 @@ constexpr int kBwdWarpsPerBlock = 2;
 
 // List entries per chunk, and the resident two-warp blocks per SM the kernel
 // is compiled for.  Up to 24 channels a chunk of 24 entries keeps a warp's
-// shared memory (10.3 KB) and registers (102) small enough for 10 blocks, 20
+// shared memory (10.3 KB) and registers (at most 102) small enough for 10 blocks, 20
 // warps, per SM (16 with 32-entry chunks); dL/dout is reloaded from its
 // shared-memory row after phase B, so it is not live through it.  Measured:
 // 32-entry chunks at 16 warps 0.480 ms, 24 at 20 warps 0.478 ms, 16 at 24
@@ -117,6 +118,10 @@ __device__ __forceinline__ float pixel_loss_grad(const BwdArgs& a, int C, bool i
 __device__ __forceinline__ void red_add_v4(float* p, float x, float y, float z, float w) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(w)
                  : "memory");
+}
+// 8-byte vector reduction (add); the address is 8-byte aligned.
+__device__ __forceinline__ void red_add_v2(float* p, float x, float y) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y) : "memory");
 }
 
 template <int TW, int TH, int NCP, int GP>
@@ -686,16 +691,19 @@ __device__ __forceinline__ void project_bwd_record(const ViewParams* __restrict_
                 if (val != 0.0f) atomicAdd(&gp.xyz[3ull * i + cc], val);
             }
         }
-        if (gp.scale) {
-            if (dsx != 0.0f) atomicAdd(&gp.scale[2ull * i], dsx);
-            if (dsy != 0.0f) atomicAdd(&gp.scale[2ull * i + 1], dsy);
+        // one vector reduction per row where the row is aligned (quaternion
+        // rows always are: the call checks 16-byte alignment)
+        if (gp.scale && (dsx != 0.0f || dsy != 0.0f)) {
+            if (((uintptr_t)gp.scale & 7u) == 0u) {
+                red_add_v2(gp.scale + 2ull * i, dsx, dsy);
+            } else {
+                atomicAdd(&gp.scale[2ull * i], dsx);
+                atomicAdd(&gp.scale[2ull * i + 1], dsy);
+            }
         }
-        if (gp.quat) {
-            atomicAdd(&gp.quat[4ull * i + 0], (dw - w * dot) * invn);
-            atomicAdd(&gp.quat[4ull * i + 1], (dx_ - qx * dot) * invn);
-            atomicAdd(&gp.quat[4ull * i + 2], (dy_ - qy * dot) * invn);
-            atomicAdd(&gp.quat[4ull * i + 3], (dz_ - qz * dot) * invn);
-        }
+        if (gp.quat)
+            red_add_v4(gp.quat + 4ull * i, (dw - w * dot) * invn, (dx_ - qx * dot) * invn, (dy_ - qy * dot) * invn,
+                       (dz_ - qz * dot) * invn);
 }
 
 __global__ void __launch_bounds__(256) project_bwd_k(const ViewParams* __restrict__ views, SurfelPtrs sp,
