@@ -25,20 +25,14 @@ struct RectTilesF {
     __device__ unsigned long long operator()(unsigned long long j) const { return rect_tiles(rects[sorted_rec[j]]); }
 };
 
-__global__ void finalize_pairs_k(StateHeader* hdr, unsigned long long cap) {
-    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
-    unsigned long long need = hdr->need_pairs;
-    hdr->n_pairs = need < cap ? need : cap;
-    if (need > cap) hdr->status |= kStatusPairOverflow;
-}
-
+// The scan's one-block pass also leaves the pair count: need_pairs, the
+// count clamped to the capacity, and the overflow bit.
 void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeader* hdr_n_records,
                 unsigned long long rec_cap, unsigned long long* pair_off, unsigned long long* tile_sums,
                 StateHeader* hdr, unsigned long long pair_cap, cudaStream_t s) {
+    const ScanTotal total{&hdr->need_pairs, &hdr->n_pairs, pair_cap, &hdr->status, kStatusPairOverflow};
     device_exclusive_scan<RectTilesF, unsigned long long>(RectTilesF{sorted_rec, rects}, &hdr_n_records->n_records,
-                                                          rec_cap, tile_sums, pair_off, &hdr->need_pairs, s);
-    launch_pdl(finalize_pairs_k, dim3(1), dim3(1), 0, s, hdr, pair_cap);
-    note_launches(1);
+                                                          rec_cap, tile_sums, pair_off, total, s);
 }
 
 // The views' first tile ids and tile columns, staged in shared memory: the
@@ -79,7 +73,7 @@ __global__ void __launch_bounds__(256) emit_pairs_k(const ViewParams* __restrict
         const int cols = s_cols[vi];
         for (int ty = y0; ty <= y1; ++ty) {
             for (int tx = x0; tx <= x1; ++tx, ++p) {
-                if (p >= pair_cap) return;  // overflow: recorded by finalize_pairs_k
+                if (p >= pair_cap) return;  // overflow: recorded by the pair scan
                 pair_keys[p] = (uint32_t)(base + (long long)ty * cols + tx);
                 pair_vals[p] = rec;
             }

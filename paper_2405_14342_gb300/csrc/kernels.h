@@ -78,7 +78,8 @@ void upload_views(const ViewsArg& va, int n_views, ViewParams* dst, StateHeader*
 // Cull + visibility bitmask: bits[v * n_words + w] bit l <=> surfel 32w+l visible in view v.
 void cull_views(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, uint32_t* bits, long long n_words,
                 cudaStream_t s);
-// Record positions: exclusive scan of popc(bits) (view-major) -> word_off; total -> hdr->need_records.
+// Record positions: exclusive scan of popc(bits) (view-major) -> word_off; total -> hdr->need_records,
+// n_records clamped to rec_cap (overflow bit in hdr->status).
 void scan_visible(const uint32_t* bits, long long n_words_total, uint32_t* word_off, uint32_t* tile_sums,
                   StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s);
 size_t scan_tile_sums_words(unsigned long long cap);
@@ -90,7 +91,8 @@ void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs 
                      uint32_t* keys, uint32_t* vals, unsigned long long rec_cap, cudaStream_t s);
 
 // ---- bin.cu
-// Pair offsets per depth-sorted record; total -> hdr->need_pairs, n_pairs clamped.
+// Pair offsets per depth-sorted record; total -> hdr->need_pairs, n_pairs clamped to pair_cap
+// (overflow bit in hdr->status).
 void scan_pairs(const uint32_t* sorted_rec, const uint2* rects, const StateHeader* hdr_n_records,
                 unsigned long long rec_cap, unsigned long long* pair_off, unsigned long long* tile_sums,
                 StateHeader* hdr, unsigned long long pair_cap, cudaStream_t s);
@@ -103,7 +105,6 @@ void emit_pairs(const ViewParams* views, int n_views, const uint32_t* sorted_rec
 void tile_ranges(const uint32_t* sorted_tile, const uint32_t* pair_rec, const Record* recs, const ViewParams* views,
                  int n_views, Consts k, const StateHeader* hdr, unsigned long long pair_cap, uint2* ranges,
                  float4* pair_mc, uint8_t* pair_blk, cudaStream_t s);
-void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s);
 // Tile order by descending list length (identity when sort_ok is false);
 // uses ka/va/kb/vb/kalt (>= n_tiles uint32 each) and the radix histogram.
 void order_tiles(const uint2* ranges, long long n_tiles, uint32_t* order, bool sort_ok, uint32_t* ka, uint32_t* va,

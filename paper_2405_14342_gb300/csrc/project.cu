@@ -311,24 +311,13 @@ struct PopcF {
 
 size_t scan_tile_sums_words(unsigned long long cap) { return (size_t)scan_tiles_for(cap) * 2 + 2; }
 
-__global__ void finalize_records_k(StateHeader* hdr, unsigned long long cap) {
-    pdl_wait();   // after the previous kernel of the stream (programmatic launch)
-    unsigned long long need = hdr->need_records;
-    hdr->n_records = need < cap ? need : cap;
-    if (need > cap) hdr->status |= kStatusRecordOverflow;
-}
-
+// The scan's one-block pass also leaves the record count: need_records, the
+// count clamped to the capacity, and the overflow bit.
 void scan_visible(const uint32_t* bits, long long n_words_total, uint32_t* word_off, uint32_t* tile_sums,
                   StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s) {
+    const ScanTotal total{&hdr->need_records, &hdr->n_records, rec_cap, &hdr->status, kStatusRecordOverflow};
     device_exclusive_scan<PopcF, uint32_t>(PopcF{bits}, nullptr, (unsigned long long)n_words_total, tile_sums,
-                                           word_off, &hdr->need_records, s);
-    launch_pdl(finalize_records_k, dim3(1), dim3(1), 0, s, hdr, rec_cap);
-    note_launches(1);
-}
-
-void finalize_records(StateHeader* hdr, unsigned long long rec_cap, cudaStream_t s) {
-    launch_pdl(finalize_records_k, dim3(1), dim3(1), 0, s, hdr, rec_cap);
-    note_launches(1);
+                                           word_off, total, s);
 }
 
 void project_records(const ViewParams* views, int n_views, Consts k, SurfelPtrs sp, const uint32_t* bits,

@@ -4,7 +4,10 @@
 // whole sequence can be captured in a CUDA graph although the real length
 // is only known on the device:
 //   1. scan_reduce_k   : per 4096-element tile, sum of f(i)
-//   2. scan_tiles_k    : one block, exclusive scan of the tile sums; writes the total
+//   2. scan_tiles_k    : one block, exclusive scan of the tile sums; writes the
+//                        total (and, when asked, the total clamped to a
+//                        capacity with an overflow bit, so that no separate
+//                        kernel has to finish the count)
 //   3. scan_down_k     : per tile, block-wide exclusive scan plus the tile offset
 // f(i) is a functor giving the value of element i (no input array needs to
 // be materialised).  No kernel waits on another block.
@@ -77,9 +80,20 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_k(F f, const unsigne
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
 }
 
-// One block: exclusive scan of n_tiles tile sums in place; *total = sum.
+// Where the one-block pass leaves the scan's total: the total itself and,
+// optionally, min(total, cap), with overflow_bit set in *status when the
+// total exceeds cap.  Null pointers are skipped.
+struct ScanTotal {
+    unsigned long long* total;
+    unsigned long long* clamped;
+    unsigned long long cap;
+    unsigned int* status;
+    unsigned int overflow_bit;
+};
+
+// One block: exclusive scan of n_tiles tile sums in place; the sum as `out` asks.
 template <class T>
-__global__ void __launch_bounds__(kScanThreads) scan_tiles_k(T* tile_sums, int n_tiles, unsigned long long* total) {
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_k(T* tile_sums, int n_tiles, ScanTotal out) {
     pdl_wait();   // after the previous kernel of the stream (programmatic launch)
     __shared__ T sh[33];
     T carry = 0;
@@ -91,7 +105,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_tiles_k(T* tile_sums, int n
         if (i < n_tiles) tile_sums[i] = carry + ex;
         carry += tot;
     }
-    if (threadIdx.x == 0 && total) *total = (unsigned long long)carry;
+    if (threadIdx.x == 0) {
+        const unsigned long long t = (unsigned long long)carry;
+        if (out.total) *out.total = t;
+        if (out.clamped) *out.clamped = t < out.cap ? t : out.cap;
+        if (out.status && t > out.cap) *out.status |= out.overflow_bit;
+    }
 }
 
 template <class F, class T>
@@ -128,7 +147,7 @@ inline int scan_tiles_for(unsigned long long cap) {
 // Launch the three-stage scan.  tile_sums must hold scan_tiles_for(cap) T.
 template <class F, class T>
 inline void device_exclusive_scan(F f, const unsigned long long* n_ptr, unsigned long long cap, T* tile_sums,
-                                  T* out, unsigned long long* total, cudaStream_t s) {
+                                  T* out, ScanTotal total, cudaStream_t s) {
     int nt = scan_tiles_for(cap);
     launch_pdl(scan_reduce_k<F, T>, dim3(nt), dim3(kScanThreads), 0, s, f, n_ptr, cap, tile_sums);
     launch_pdl(scan_tiles_k<T>, dim3(1), dim3(kScanThreads), 0, s, tile_sums, nt, total);
